@@ -1,0 +1,263 @@
+"""Pins for the FP64 oracle: facts the paper and the mathematics fix, independent of the
+oracle's own eigendecomposition route.
+
+* dense pattern  -> every row is column j of the full A^(-1/p) (Sec. 3: no truncation),
+  checked with Schur-Pade ``fractional_matrix_power`` and, for p=1, Cholesky solves;
+* block-diagonal -> blockwise A^(-1/p);
+* diagonal A     -> a_jj^(-1/p);
+* 4-node chain, p=1 -> exact rationals worked by hand from Alg. 1/2;
+* 2x2 submatrices -> the closed-form square root of a 2x2 SPD matrix;
+* invariants (F^p S = I, F = F^T), scaling, permutation equivariance;
+* tiny random cases against a 40-digit mpmath eigen-solver;
+* the paper's Alg. 2 column assembly written out with dense loops (layout pin);
+* the gradient against central differences and the Frechet block identity
+  f([[S,E],[0,S]]) = [[f(S), L_f(S,E)],[0,f(S)]].
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+import oracle
+import workloads as wl
+
+
+def _dense_spd(n, seed, shift=1.0):
+    rng = np.random.default_rng(seed)
+    b = rng.standard_normal((n, n))
+    return b @ b.T / n + shift * np.eye(n)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_dense_pattern_is_full_inverse_root(p):
+    a = _dense_spd(24, seed=p)
+    csr = wl.dense_to_csr(a, keep=np.ones_like(a, dtype=bool))
+    y = oracle.invroot(csr.rowptr, csr.colind, csr.vals, p)
+    full = np.real(sl.fractional_matrix_power(a, -1.0 / p))
+    ydense = oracle.to_dense(csr.n, csr.rowptr, csr.colind, y)
+    np.testing.assert_allclose(ydense, full.T, rtol=0, atol=1e-12)
+    if p == 1:
+        c = sl.cho_factor(a)
+        np.testing.assert_allclose(ydense, sl.cho_solve(c, np.eye(24)).T, atol=1e-12)
+    # the paper's residual (Sec. 4.1) vanishes when nothing is truncated
+    assert oracle.residual_2norm(a, ydense, p) < 1e-11
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_block_diagonal_is_blockwise_root(p):
+    sizes = [1, 3, 7, 4]
+    blocks = [_dense_spd(s, seed=10 + s) for s in sizes]
+    a = sl.block_diag(*blocks)
+    keep = sl.block_diag(*[np.ones((s, s), dtype=bool) for s in sizes])
+    csr = wl.dense_to_csr(a, keep=keep)
+    y = oracle.to_dense(csr.n, csr.rowptr, csr.colind,
+                        oracle.invroot(csr.rowptr, csr.colind, csr.vals, p))
+    expect = sl.block_diag(*[np.real(sl.fractional_matrix_power(b, -1.0 / p)) for b in blocks])
+    np.testing.assert_allclose(y, expect.T, atol=1e-12)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5])
+def test_diagonal_matrix(p):
+    d = np.array([0.5, 2.0, 3.0, 10.0, 1e-3])
+    csr = wl.dense_to_csr(np.diag(d))
+    y = oracle.invroot(csr.rowptr, csr.colind, csr.vals, p)
+    np.testing.assert_allclose(y, d ** (-1.0 / p), rtol=1e-14)
+
+
+def test_chain4_p1_exact_rationals():
+    # A = tridiag(1, 2, 1), n=4.  Hand-worked from Alg. 1 and Alg. 2:
+    #  row 0: R={0,1}, S=[[2,1],[1,2]], S^-1=(1/3)[[2,-1],[-1,2]], pos 0 -> (2/3, -1/3)
+    #  row 1: R={0,1,2}, S=tridiag(1,2,1) 3x3, det 4,
+    #         S^-1=(1/4)[[3,-2,1],[-2,4,-2],[1,-2,3]], pos 1 -> (-1/2, 1, -1/2)
+    #  row 2: R={1,2,3}, same S, pos 1                      -> (-1/2, 1, -1/2)
+    #  row 3: R={2,3}, 2x2 as row 0, pos 1                  -> (-1/3, 2/3)
+    expect = [Fraction(2, 3), Fraction(-1, 3),
+              Fraction(-1, 2), Fraction(1), Fraction(-1, 2),
+              Fraction(-1, 2), Fraction(1), Fraction(-1, 2),
+              Fraction(-1, 3), Fraction(2, 3)]
+    a = 2 * np.eye(4) + np.eye(4, k=1) + np.eye(4, k=-1)
+    csr = wl.dense_to_csr(a)
+    assert csr.rowptr.tolist() == [0, 2, 5, 8, 10]
+    y = oracle.invroot(csr.rowptr, csr.colind, csr.vals, 1)
+    np.testing.assert_allclose(y, [float(f) for f in expect], atol=1e-15)
+
+
+def _inv_sqrt_2x2(s):
+    # sqrt(S) = (S + sqrt(det) I) / sqrt(tr + 2 sqrt(det)) for 2x2 SPD S
+    det = s[0, 0] * s[1, 1] - s[0, 1] * s[1, 0]
+    r = (s + np.sqrt(det) * np.eye(2)) / np.sqrt(np.trace(s) + 2 * np.sqrt(det))
+    dr = r[0, 0] * r[1, 1] - r[0, 1] * r[1, 0]
+    return np.array([[r[1, 1], -r[0, 1]], [-r[1, 0], r[0, 0]]]) / dr
+
+
+def test_chain_end_rows_2x2_closed_form_p2():
+    rng = np.random.default_rng(3)
+    n = 9
+    off = rng.uniform(-0.9, 0.9, n - 1)
+    a = np.diag(rng.uniform(2.0, 3.0, n)) + np.diag(off, 1) + np.diag(off, -1)
+    csr = wl.dense_to_csr(a)
+    y = oracle.invroot(csr.rowptr, csr.colind, csr.vals, 2)
+    f0 = _inv_sqrt_2x2(a[:2, :2])
+    np.testing.assert_allclose(y[0:2], f0[:, 0], atol=1e-14)
+    fl = _inv_sqrt_2x2(a[-2:, -2:])
+    np.testing.assert_allclose(y[-2:], fl[:, 1], atol=1e-14)
+    # interior rows: 3x3 submatrix whose corner A[j-1][j+1] is not stored -> zero
+    for j in range(1, n - 1):
+        s = a[j - 1:j + 2, j - 1:j + 2].copy()
+        assert s[0, 2] == 0.0
+        f = np.real(sl.fractional_matrix_power(s, -0.5))
+        np.testing.assert_allclose(y[csr.rowptr[j]:csr.rowptr[j + 1]], f[:, 1], atol=1e-13)
+
+
+def test_unstored_entries_are_zero_in_submatrix():
+    # A dense matrix whose pattern is banded: entries outside the stored band must be
+    # treated as zero even though the dense array holds values there.
+    a = _dense_spd(10, seed=5, shift=3.0)
+    keep = np.abs(np.subtract.outer(np.arange(10), np.arange(10))) <= 2
+    csr = wl.dense_to_csr(a, keep=keep)
+    for j in [0, 4, 9]:
+        s, r, pos = oracle.submatrix(csr.rowptr, csr.colind, csr.vals, j)
+        expect = np.where(keep, a, 0.0)[np.ix_(r, r)]
+        np.testing.assert_array_equal(s, expect)
+        assert r[pos] == j
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_alg2_column_assembly_layout(p):
+    # Alg. 2 written out with dense loops: X[R[i]][j] = f(S_j)[i][R.indexof(j)];
+    # the row-based CSR result is X transposed (Sec. 3.4).
+    a0 = wl.random_sparse_spd(12, 0.3, seed=7)
+    a = oracle.to_dense(a0.n, a0.rowptr, a0.colind, a0.vals)
+    n = a.shape[0]
+    x = np.zeros((n, n))
+    for j in range(n):
+        r = [i for i in range(n) if a[i][j] != 0]
+        s = np.array([[a[r[k]][r[l]] for l in range(len(r))] for k in range(len(r))])
+        f = np.real(sl.fractional_matrix_power(s, -1.0 / p))
+        for i in range(len(r)):
+            x[r[i]][j] = f[i][r.index(j)]
+    y = oracle.to_dense(n, a0.rowptr, a0.colind,
+                        oracle.invroot(a0.rowptr, a0.colind, a0.vals, p))
+    np.testing.assert_allclose(y, x.T, atol=1e-12)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_submatrix_invariants(p):
+    a = wl.overlap_small(n=400)
+    for j in range(0, 400, 37):
+        s, r, pos = oracle.submatrix(a.rowptr, a.colind, a.vals, j)
+        f = oracle.inv_root(s, p)
+        np.testing.assert_allclose(f, f.T, atol=1e-13)
+        resid = np.linalg.matrix_power(f, p) @ s - np.eye(len(r))
+        assert np.abs(resid).max() < 1e-12 * np.linalg.cond(s)
+        np.testing.assert_allclose(oracle.inv_root_column(s, pos, p), f[:, pos], atol=1e-14)
+        assert np.linalg.eigvalsh(f).min() > 0
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_scaling(p):
+    a = wl.overlap_small(n=300)
+    y1 = oracle.invroot(a.rowptr, a.colind, a.vals, p)
+    y2 = oracle.invroot(a.rowptr, a.colind, 7.5 * a.vals, p)
+    np.testing.assert_allclose(y2, 7.5 ** (-1.0 / p) * y1, rtol=1e-12,
+                               atol=1e-13 * np.abs(y1).max())
+
+
+def test_permutation_equivariance():
+    a0 = wl.random_sparse_spd(15, 0.25, seed=11)
+    a = oracle.to_dense(a0.n, a0.rowptr, a0.colind, a0.vals)
+    perm = np.random.default_rng(2).permutation(15)
+    b = a[np.ix_(perm, perm)]
+    cb = wl.dense_to_csr(b)
+    ya = oracle.to_dense(15, a0.rowptr, a0.colind, oracle.invroot(a0.rowptr, a0.colind, a0.vals, 2))
+    yb = oracle.to_dense(15, cb.rowptr, cb.colind, oracle.invroot(cb.rowptr, cb.colind, cb.vals, 2))
+    np.testing.assert_allclose(yb, ya[np.ix_(perm, perm)], atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_bruteforce_mpmath(p):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    for seed in range(3):
+        a0 = wl.random_sparse_spd(7, 0.4, seed=seed)
+        y = oracle.invroot(a0.rowptr, a0.colind, a0.vals, p)
+        for j in range(a0.n):
+            s, r, pos = oracle.submatrix(a0.rowptr, a0.colind, a0.vals, j)
+            lam, v = mp.eigsy(mp.matrix(s.tolist()))
+            m = len(r)
+            col = [sum(v[k, i] * lam[i] ** (mp.mpf(-1) / p) * v[pos, i] for i in range(m))
+                   for k in range(m)]
+            np.testing.assert_allclose(y[a0.rowptr[j]:a0.rowptr[j + 1]],
+                                       [float(c) for c in col], rtol=0, atol=1e-14)
+
+
+def test_plan_bruteforce():
+    for seed in range(4):
+        a0 = wl.random_sparse_spd(20, 0.2, seed=seed)
+        dense = oracle.to_dense(a0.n, a0.rowptr, a0.colind, np.ones(a0.nnz))
+        m, pos = oracle.plan(a0.rowptr, a0.colind)
+        for j in range(a0.n):
+            r = [i for i in range(a0.n) if dense[j][i] != 0]
+            assert m[j] == len(r)
+            assert pos[j] == r.index(j)
+
+
+def test_missing_diagonal_and_indefinite_are_errors():
+    a = np.array([[0.0, 1.0], [1.0, 2.0]])
+    csr = wl.dense_to_csr(a, keep=(a != 0))
+    with pytest.raises(ValueError):
+        oracle.plan(csr.rowptr, csr.colind)
+    b = np.array([[1.0, 2.0], [2.0, 1.0]])        # eigenvalues 3, -1
+    cb = wl.dense_to_csr(b)
+    with pytest.raises(ValueError):
+        oracle.invroot(cb.rowptr, cb.colind, cb.vals, 2)
+
+
+def test_divided_differences_match_plain_quotient():
+    lam = np.array([0.3, 0.9, 2.5, 7.0])
+    for p in (1, 2, 3):
+        g = oracle.divided_differences(lam, p)
+        f = lam ** (-1.0 / p)
+        for a in range(4):
+            for b in range(4):
+                if a == b:
+                    assert np.isclose(g[a, a], -(1.0 / p) * lam[a] ** (-1.0 / p - 1), rtol=1e-14)
+                else:
+                    assert np.isclose(g[a, b], (f[a] - f[b]) / (lam[a] - lam[b]), rtol=1e-12)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_submatrix_grad_frechet_block_identity(p):
+    rng = np.random.default_rng(20 + p)
+    m = 7
+    s = _dense_spd(m, seed=p, shift=0.7)
+    g = rng.standard_normal(m)
+    pos = 3
+    e = rng.standard_normal((m, m))
+    e = e + e.T
+    z = np.block([[s, e], [np.zeros((m, m)), s]])
+    lf = np.real(sl.fractional_matrix_power(z, -1.0 / p))[:m, m:]   # L_f(S, E)
+    lhs = np.sum(oracle.submatrix_grad(s, pos, g, p) * e)
+    rhs = g @ lf[:, pos]
+    assert abs(lhs - rhs) < 1e-11 * max(1.0, abs(rhs))
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_grad_central_differences(p):
+    a = wl.overlap_uniform(n=300, kappa=50.0)
+    w = wl.random_on_pattern(a, seed=1)
+    gr = oracle.grad(a.rowptr, a.colind, a.vals, p, w)
+
+    def loss(v):
+        return float(np.dot(w, oracle.invroot(a.rowptr, a.colind, v, p)))
+
+    h = 1e-6
+    for seed in range(3):
+        e = wl.random_on_pattern(a, seed=100 + seed, symmetric=True)
+        e /= np.linalg.norm(e)
+        fd = (loss(a.vals + h * e) - loss(a.vals - h * e)) / (2 * h)
+        assert abs(fd - gr @ e) <= 1e-6 * max(1.0, abs(fd))
+    # symmetric: the (r,c) and (c,r) entries carry the same value
+    d = oracle.to_dense(a.n, a.rowptr, a.colind, gr)
+    np.testing.assert_allclose(d, d.T, atol=1e-13)

@@ -1,0 +1,193 @@
+"""Seeded synthetic inputs for the submatrix method (inputs only, no method arithmetic).
+
+Shared by the oracle's tests, the GPU parity tests and ``bench.py``.  Nothing here
+computes a submatrix, an inverse root or anything else of the method; it only builds
+sparse symmetric matrices in CSR form (int32 ``rowptr``/``colind``, float64 ``vals``)
+and random arrays of the shapes the method consumes.
+
+The paper's own inputs (MATLAB ``sprandsym`` matrices, DFT overlap matrices,
+SuiteSparse matrices; Sec. 4.1, 4.3, 4.4) are not available, so Gaussian-overlap
+matrices stand in for them: points in a 3-D box, ``A_ij = exp(-r_ij^2 / 0.01)`` for
+``r_ij < r_c`` (the sparsity of an overlap matrix of localised basis functions, the
+paper's motivating application in Sec. 4.3), plus a diagonal that sets the condition
+number.
+
+Recipes (numpy PCG64, seed 0 unless stated):
+
+* ``overlap_small``  n=2000 points U[0,1]^3, r_c=0.12, diagonal 1.5 (p=2, FP64).
+* ``overlap_uniform`` n=32768 points U[0,L]^3 with L=1.0585 (about 177 stored
+  entries per row), diagonal shift giving kappa(A) ~ 1e3.
+* ``overlap_clustered`` n=131072 points in a periodic box of side 2: 85 % drawn from
+  64 isotropic Gaussian clusters (std 0.1), 15 % uniform; minimum-image distances;
+  kappa ~ 1e3.  Row sizes range 7..1113.
+* ``overlap_grad`` n=16384 points U[0,0.9247]^3 (about 130 entries per row), kappa ~ 1e3.
+
+Every generator can also be scaled down (``n=``) for fast tests; the box side is then
+rescaled so the expected number of neighbours stays the same.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as sla
+import scipy.spatial
+
+GAUSS_WIDTH = 0.01      # A_ij = exp(-r^2 / GAUSS_WIDTH)
+CUTOFF = 0.12           # r_c
+
+
+@dataclasses.dataclass
+class CSR:
+    """A sparse symmetric matrix in CSR form (sorted, unique column indices)."""
+    n: int
+    rowptr: np.ndarray      # int32 [n+1]
+    colind: np.ndarray      # int32 [nnz]
+    vals: np.ndarray        # float64 [nnz]
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colind.shape[0])
+
+    def row_sizes(self) -> np.ndarray:
+        return np.diff(self.rowptr).astype(np.int64)
+
+    def to_scipy(self) -> sp.csr_matrix:
+        return sp.csr_matrix((self.vals, self.colind, self.rowptr), shape=(self.n, self.n))
+
+
+def _from_pairs(n, pairs, offvals, diag, name) -> CSR:
+    i = np.concatenate([pairs[:, 0], pairs[:, 1], np.arange(n)])
+    j = np.concatenate([pairs[:, 1], pairs[:, 0], np.arange(n)])
+    v = np.concatenate([offvals, offvals, np.full(n, float(diag))])
+    m = sp.csr_matrix((v, (i, j)), shape=(n, n))
+    m.sum_duplicates()
+    m.sort_indices()
+    return CSR(n, m.indptr.astype(np.int32), m.indices.astype(np.int32),
+               m.data.astype(np.float64), name)
+
+
+def _pairs(points, cutoff, box=None):
+    tree = scipy.spatial.cKDTree(points, boxsize=box)
+    pairs = tree.query_pairs(cutoff, output_type="ndarray").astype(np.int64)
+    d = points[pairs[:, 0]] - points[pairs[:, 1]]
+    if box is not None:
+        d -= box * np.round(d / box)
+    r2 = (d * d).sum(1)
+    return pairs, np.exp(-r2 / GAUSS_WIDTH)
+
+
+def _extreme_eigs(n, pairs, offvals, seed=0):
+    """Extreme eigenvalues of the zero-diagonal part (ARPACK Lanczos, seeded start)."""
+    i = np.concatenate([pairs[:, 0], pairs[:, 1]])
+    j = np.concatenate([pairs[:, 1], pairs[:, 0]])
+    off = sp.csr_matrix((np.concatenate([offvals, offvals]), (i, j)), shape=(n, n))
+    v0 = np.random.default_rng(seed).standard_normal(n)
+    hi = sla.eigsh(off, k=1, which="LA", v0=v0, tol=1e-8, return_eigenvectors=False)[0]
+    # smallest eigenvalue via the largest of (hi*I - off), better separated for Lanczos
+    lo = hi - sla.eigsh(hi * sp.identity(n, format="csr") - off, k=1, which="LA", v0=v0,
+                        tol=1e-8, return_eigenvectors=False)[0]
+    return float(lo), float(hi)
+
+
+def diag_for_kappa(lo: float, hi: float, kappa: float) -> float:
+    """Diagonal value d with (hi + d) / (lo + d) = kappa."""
+    return (hi - kappa * lo) / (kappa - 1.0)
+
+
+def overlap_small(n: int = 2000, seed: int = 0, diag: float = 1.5) -> CSR:
+    """n points U[0,1]^3 (non-periodic), r_c = 0.12, literal diagonal 1 + 0.5."""
+    rng = np.random.default_rng(seed)
+    side = (n / 2000.0) ** (1.0 / 3.0)
+    pts = rng.uniform(0.0, side, (n, 3))
+    pairs, v = _pairs(pts, CUTOFF)
+    return _from_pairs(n, pairs, v, diag, f"overlap_small(n={n})")
+
+
+def _uniform_side(n, per_row):
+    # expected neighbours inside the cutoff ball = n / L^3 * 4/3 pi r_c^3
+    return (n * (4.0 / 3.0) * np.pi * CUTOFF ** 3 / per_row) ** (1.0 / 3.0)
+
+
+def overlap_uniform(n: int = 32768, seed: int = 0, kappa: float = 1e3,
+                    per_row: float = 200.0, side: float | None = None) -> CSR:
+    """Uniform points in a cube sized for about ``per_row`` neighbours; kappa via the diagonal."""
+    rng = np.random.default_rng(seed)
+    if side is None:
+        side = _uniform_side(n, per_row)
+    pts = rng.uniform(0.0, side, (n, 3))
+    pairs, v = _pairs(pts, CUTOFF)
+    lo, hi = _extreme_eigs(n, pairs, v, seed)
+    d = diag_for_kappa(lo, hi, kappa)
+    return _from_pairs(n, pairs, v, d, f"overlap_uniform(n={n},kappa={kappa:g})")
+
+
+def overlap_grad(n: int = 16384, seed: int = 0, kappa: float = 1e3) -> CSR:
+    """The differentiation workload: n=16384 in U[0,0.9247]^3 (about 130 per row)."""
+    side = 0.9247 * (n / 16384.0) ** (1.0 / 3.0)
+    return overlap_uniform(n, seed, kappa, side=side)
+
+
+def overlap_clustered(n: int = 131072, seed: int = 0, kappa: float = 1e3,
+                      clusters: int = 64, frac_clustered: float = 0.85) -> CSR:
+    """Gaussian-mixture points in a periodic box: uneven row sizes (7..1113 at n=131072)."""
+    rng = np.random.default_rng(seed)
+    side = 2.0 * (n / 131072.0) ** (1.0 / 3.0)
+    nc = int(frac_clustered * n)
+    centres = rng.uniform(0.0, side, (clusters, 3))
+    labels = rng.integers(0, clusters, nc)
+    pts = np.concatenate([centres[labels] + rng.normal(0.0, 0.05 * side, (nc, 3)),
+                          rng.uniform(0.0, side, (n - nc, 3))]) % side
+    pairs, v = _pairs(pts, CUTOFF, box=side)
+    lo, hi = _extreme_eigs(n, pairs, v, seed)
+    d = diag_for_kappa(lo, hi, kappa)
+    return _from_pairs(n, pairs, v, d, f"overlap_clustered(n={n},kappa={kappa:g})")
+
+
+def random_sparse_spd(n: int, density: float, seed: int = 0, margin: float = 0.5) -> CSR:
+    """Small random symmetric sparse matrix made SPD by diagonal dominance plus ``margin``.
+
+    Used for brute-force and edge-case tests (tiny n)."""
+    rng = np.random.default_rng(seed)
+    mask = np.triu(rng.random((n, n)) < density, 1)
+    vals = rng.uniform(-1.0, 1.0, (n, n)) * mask
+    dense = vals + vals.T
+    dense += np.diag(np.abs(dense).sum(1) + margin)
+    return dense_to_csr(dense, f"random_sparse_spd(n={n})")
+
+
+def dense_to_csr(dense: np.ndarray, name: str = "", keep=None) -> CSR:
+    """CSR of a dense matrix; the stored pattern is ``keep`` (default: nonzeros + diagonal)."""
+    n = dense.shape[0]
+    if keep is None:
+        keep = (dense != 0) | np.eye(n, dtype=bool)
+    # store explicit zeros that ``keep`` asks for
+    r, c = np.nonzero(keep)
+    m = sp.csr_matrix((dense[r, c], (r, c)), shape=(n, n))
+    m.sort_indices()
+    return CSR(n, m.indptr.astype(np.int32), m.indices.astype(np.int32),
+               m.data.astype(np.float64), name)
+
+
+def random_on_pattern(a: CSR, seed: int, symmetric: bool = False) -> np.ndarray:
+    """N(0,1) values on A's pattern (length nnz); optionally symmetrised (E_rc = E_cr)."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal(a.nnz)
+    if symmetric:
+        m = sp.csr_matrix((w, a.colind, a.rowptr), shape=(a.n, a.n))
+        m = (m + m.T) * 0.5
+        m = m.tocsr()
+        m.sort_indices()
+        # same pattern (A's pattern is symmetric), so data lines up with colind
+        assert m.nnz == a.nnz and np.array_equal(m.indices, a.colind)
+        w = m.data.copy()
+    return w
+
+
+WORKLOADS = {
+    "overlap_small": overlap_small,
+    "overlap_uniform": overlap_uniform,
+    "overlap_clustered": overlap_clustered,
+    "overlap_grad": overlap_grad,
+}
