@@ -1,0 +1,182 @@
+/*
+ * submat.h -- C ABI of the GB300 submatrix-method library (libsubmat.so).
+ *
+ * The submatrix method (Lass et al., PASC'18, Sec. 3) approximates A^(-1/p) for a large
+ * sparse symmetric positive definite matrix A while keeping A's sparsity pattern:
+ *
+ *   Algorithm 1 (Sec. 3.1): for every row j, R_j = the stored column indices of row j
+ *       (ascending), S_j[k][l] = A[R_j[k]][R_j[l]] (zero where not stored).
+ *   Sec. 3.2: F_j = S_j^(-1/p), the principal inverse p-th root of S_j.
+ *   Algorithm 2 (Sec. 3.3) with the row-based CSR storage of Sec. 3.4: the result has A's
+ *       rowptr/colind, and row j holds column pos_j = R_j.indexof(j) of F_j.
+ *
+ * All calls return a submat_status and never throw or abort.  Value arrays are FP64 and
+ * in A's CSR order.  Device pointers are CUDA device (or managed) memory of the device
+ * that was current when the plan was made; the caller owns them.  Calls are ordered on
+ * the stream passed in (a cudaStream_t, NULL = legacy default stream); a plan must not be
+ * used from two streams at the same time.
+ */
+#ifndef SUBMAT_H
+#define SUBMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SUBMAT_API __attribute__((visibility("default")))
+#else
+#define SUBMAT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SUBMAT_OK = 0,
+  SUBMAT_EINVAL = 1,    /* bad argument: NULL pointer, p < 1, unsorted/duplicate/out-of-range
+                           column index, negative sizes, vals_out aliasing vals_in        */
+  SUBMAT_ENODIAG = 2,   /* a row does not store its diagonal entry (Alg. 2 needs
+                           R.indexof(j))                                                  */
+  SUBMAT_ENOTSYM = 3,   /* the pattern is not symmetric                                    */
+  SUBMAT_ETOOBIG = 4,   /* a row has more entries than SUBMAT_MAX_M                        */
+  SUBMAT_ENOMEM = 5,    /* a device or host allocation failed                              */
+  SUBMAT_ECUDA = 6,     /* a CUDA runtime call failed (the message is in submat_last_error) */
+  SUBMAT_ENOTSPD = 7,   /* some submatrix is not positive definite or holds a non-finite
+                           value; its output row is NaN, the others are valid            */
+  SUBMAT_ENOFWD = 8     /* backward called before any forward on this plan                 */
+} submat_status;
+
+/* Largest submatrix order (row length) the library accepts. */
+#define SUBMAT_MAX_M 1536
+
+/* Precision of the submatrix operation. */
+enum {
+  SUBMAT_PREC_FP64 = 0,       /* coupled Newton iteration entirely in FP64 (CUDA cores)     */
+  SUBMAT_PREC_MIXED_F16 = 1   /* coupled Newton iteration on the tensor cores with operands
+                                 split into FP16 hi/lo pairs (three products per GEMM, FP32
+                                 accumulation), then an FP64 column refinement and check  */
+};
+
+typedef struct {
+  int32_t n;               /* order of A                                                 */
+  int64_t nnz;             /* stored entries                                             */
+  const int32_t* rowptr;   /* [n+1], rowptr[0] = 0, nondecreasing, rowptr[n] = nnz        */
+  const int32_t* colind;   /* [nnz], strictly ascending within each row, in [0, n)        */
+  int32_t on_device;       /* 0: host pointers, 1: device pointers                       */
+} submat_csr;
+
+typedef struct {
+  int32_t precision;       /* SUBMAT_PREC_*; default SUBMAT_PREC_MIXED_F16               */
+  int32_t k_max;           /* iteration cap of the coupled iteration; default 40         */
+  double tol;              /* stop when ||M - I||_F <= tol * sqrt(m) (or when it stops
+                              decreasing below 1e-2 sqrt(m)), then do one more X update;
+                              default 1e-4 (mixed) / 1e-7 (FP64); <= 0 selects the default */
+  double resid_tol;        /* a row whose FP64 column residual ||e_pos - F^p s_pos||_2
+                              exceeds this goes to the FP64 eigendecomposition fallback;
+                              default 1e-3                                                */
+  int32_t refine_steps;    /* FP64 column refinement: p = 1: iterative-refinement sweeps
+                              (default 2); p >= 2: 1 = one Newton step on the column,
+                              0 = none (default 0: once the iteration has converged the
+                              step amplifies the part of the error that does not commute
+                              with S_j); < 0 selects the default                          */
+  int32_t use_graph;       /* capture the forward launches into a CUDA graph; default 1  */
+  double kappa_max;        /* mixed path: a row whose condition estimate
+                              lambda_bar / lambda_min (power iteration on the converged
+                              iterate) exceeds this goes to the FP64 fallback; default 100 */
+} submat_opts;
+
+typedef struct {
+  int64_t n_rows;          /* submatrices processed by the last forward                  */
+  int32_t m_max;           /* largest submatrix order                                    */
+  int32_t iters_max;       /* largest iteration count of the last forward                */
+  int64_t iters_sum;       /* sum of iteration counts                                    */
+  int64_t n_fallback;      /* rows recomputed by the FP64 eigendecomposition fallback    */
+  int64_t n_notspd;        /* rows with a non-positive eigenvalue or non-finite input    */
+  double max_resid;        /* largest FP64 column residual seen before the fallback      */
+  double sum_m3;           /* sum over rows of m^3 (true sizes)                           */
+  double flops_tensor;     /* tensor-core flops executed by the last forward, counted as
+                              sum_j iters_j * (p+1) * 2 m_j^3 * products (true m_j)      */
+  double flops_fp64;       /* FP64 flops of the last forward (FP64 path: iterations;
+                              mixed path: column refinement; both: fallback)             */
+  float ms_kernel;         /* device time of the last forward's main (Newton) kernel,
+                              from CUDA events recorded around it on the launch stream   */
+  float ms_fallback;       /* device time of the last forward's fallback kernel          */
+  int64_t n_illcond;       /* rows sent to the fallback by the condition estimate        */
+} submat_report;
+
+typedef struct submat_plan_s* submat_plan_t;
+
+/* Fill *opts with the defaults. */
+SUBMAT_API void submat_default_opts(submat_opts* opts);
+
+/*
+ * Build a plan for A's pattern and the root order p >= 1 (Alg. 1, index part).
+ * Checks the pattern (SUBMAT_EINVAL / ENODIAG / ENOTSYM / ETOOBIG), computes m_j and
+ * pos_j on the device, orders the rows by decreasing m_j for the persistent scheduler,
+ * and allocates the per-CTA working storage.  The plan keeps device copies of rowptr and
+ * colind; the caller's arrays may be freed afterwards.  opts may be NULL (defaults).
+ */
+SUBMAT_API submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* opts,
+                          submat_plan_t* out);
+
+/*
+ * Forward: vals_out = the submatrix method's approximation of A^(-1/p) on A's pattern
+ * (Alg. 1, Sec. 3.2, Alg. 2).  vals_in and vals_out are device arrays of nnz doubles in
+ * CSR order; they must not overlap.  A's values must be symmetric (A[r][c] = A[c][r]).
+ * The plan keeps a device copy of vals_in for the backward.  Returns SUBMAT_ENOTSPD (after
+ * writing every other row) when some submatrix is not positive definite.  Stream-ordered;
+ * the status of the numerics (ENOTSPD) needs a stream synchronisation and is only
+ * returned when sync != 0; with sync == 0 the call returns SUBMAT_OK after queueing the
+ * work and submat_get_report gives the counts later.
+ */
+SUBMAT_API submat_status submat_invroot(submat_plan_t plan, const double* vals_in, double* vals_out,
+                             void* stream, int32_t sync);
+
+/*
+ * Forward on host buffers: copies vals_in (nnz doubles, host memory; pinned memory makes
+ * the copies asynchronous) to plan-owned device memory on the stream, runs
+ * submat_invroot, copies the result back into vals_out (host, nnz doubles) and
+ * synchronises the stream.  The device buffers are allocated on the first call and kept
+ * by the plan.  Returns SUBMAT_ENOTSPD like submat_invroot with sync != 0.
+ */
+SUBMAT_API submat_status submat_invroot_host(submat_plan_t plan, const double* vals_in,
+                                             double* vals_out, void* stream);
+
+/*
+ * Backward (Daleckii-Krein adjoint; Higham, Functions of Matrices, Thm. 3.11):
+ * grad_in = dL/dvals for L = sum(grad_out * vals_out) of the last forward, with respect to
+ * A's stored values, the (r,c)/(c,r) pair sharing one symmetric perturbation.  For each row
+ * j the submatrix is regathered from the saved vals_in and decomposed again in FP64
+ * (recomputation, no stored iterates).  grad_out and grad_in are device arrays of nnz
+ * doubles; grad_in is overwritten.  Returns SUBMAT_ENOFWD if no forward ran on this plan.
+ */
+SUBMAT_API submat_status submat_invroot_backward(submat_plan_t plan, const double* grad_out,
+                                      double* grad_in, void* stream);
+
+/* Counters of the last forward (synchronises the plan's stream). */
+SUBMAT_API submat_status submat_get_report(submat_plan_t plan, submat_report* out);
+
+/*
+ * The integer plan as computed on the device (Alg. 1 index part): m[j] = |R_j| and
+ * pos[j] = R_j.indexof(j), copied into the caller's host arrays of n int32 each.
+ */
+SUBMAT_API submat_status submat_plan_rows(submat_plan_t plan, int32_t* m, int32_t* pos);
+
+/* Order n and entry count nnz of the plan's pattern. */
+SUBMAT_API submat_status submat_plan_shape(submat_plan_t plan, int32_t* n, int64_t* nnz);
+
+/* Release every resource of the plan.  NULL is ignored. */
+SUBMAT_API void submat_plan_destroy(submat_plan_t plan);
+
+/* Static description of a status code. */
+SUBMAT_API const char* submat_status_string(submat_status s);
+
+/* Message of the last failing call on this thread ("" if none). */
+SUBMAT_API const char* submat_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SUBMAT_H */

@@ -1,0 +1,275 @@
+"""GB300 submatrix method: A^(-1/p) of a sparse SPD matrix on A's own sparsity pattern.
+
+Thin Python binding of ``libsubmat.so`` (C ABI in ``include/submat.h``): argument
+marshalling only, every step of the computation runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams.  There is no CPU fallback: if the library is
+missing or no GPU is present, the calls raise.
+
+    plan = submat_plan(rowptr, colind, p=2)              # Alg. 1 index part, on the GPU
+    y = submat_invroot(plan, vals)                       # Alg. 1, Sec. 3.2, Alg. 2
+    g = submat_invroot_backward(plan, grad_y)            # Daleckii-Krein adjoint
+    y = SubmatInvRoot.apply(vals, plan)                  # autograd
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsubmat.so")
+
+SUBMAT_MAX_M = 1536
+PREC_FP64 = 0
+PREC_MIXED_F16 = 1
+
+STATUS = {
+    0: "SUBMAT_OK", 1: "SUBMAT_EINVAL", 2: "SUBMAT_ENODIAG", 3: "SUBMAT_ENOTSYM",
+    4: "SUBMAT_ETOOBIG", 5: "SUBMAT_ENOMEM", 6: "SUBMAT_ECUDA", 7: "SUBMAT_ENOTSPD",
+    8: "SUBMAT_ENOFWD",
+}
+
+
+class SubmatError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class CSR(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p),
+                ("on_device", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("k_max", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("resid_tol", ctypes.c_double),
+                ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("kappa_max", ctypes.c_double)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("m_max", ctypes.c_int32),
+                ("iters_max", ctypes.c_int32), ("iters_sum", ctypes.c_int64),
+                ("n_fallback", ctypes.c_int64), ("n_notspd", ctypes.c_int64),
+                ("max_resid", ctypes.c_double), ("sum_m3", ctypes.c_double),
+                ("flops_tensor", ctypes.c_double), ("flops_fp64", ctypes.c_double),
+                ("ms_kernel", ctypes.c_float), ("ms_fallback", ctypes.c_float),
+                ("n_illcond", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["submat_default_opts", "submat_plan", "submat_invroot", "submat_invroot_host",
+           "submat_invroot_backward",
+           "submat_get_report", "submat_plan_rows", "submat_plan_shape", "submat_plan_destroy",
+           "submat_status_string", "submat_last_error"]
+
+_lib_handle = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libsubmat.so (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with paper_1710_10899_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    lib.submat_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.submat_default_opts.restype = None
+    lib.submat_plan.argtypes = [ctypes.POINTER(CSR), i32, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
+    lib.submat_plan.restype = i32
+    lib.submat_invroot.argtypes = [vp, vp, vp, vp, i32]
+    lib.submat_invroot.restype = i32
+    lib.submat_invroot_host.argtypes = [vp, vp, vp, vp]
+    lib.submat_invroot_host.restype = i32
+    lib.submat_invroot_backward.argtypes = [vp, vp, vp, vp]
+    lib.submat_invroot_backward.restype = i32
+    lib.submat_get_report.argtypes = [vp, ctypes.POINTER(Report)]
+    lib.submat_get_report.restype = i32
+    lib.submat_plan_rows.argtypes = [vp, vp, vp]
+    lib.submat_plan_rows.restype = i32
+    lib.submat_plan_shape.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64)]
+    lib.submat_plan_shape.restype = i32
+    lib.submat_plan_destroy.argtypes = [vp]
+    lib.submat_plan_destroy.restype = None
+    lib.submat_status_string.argtypes = [i32]
+    lib.submat_status_string.restype = ctypes.c_char_p
+    lib.submat_last_error.argtypes = []
+    lib.submat_last_error.restype = ctypes.c_char_p
+    _lib_handle = lib
+    return lib
+
+
+def _check(lib, st):
+    if st != 0:
+        raise SubmatError(st, lib.submat_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A plan for one sparsity pattern and root order p (``submat_plan``)."""
+
+    def __init__(self, rowptr, colind, p: int, precision: str = "mixed", k_max: int = 0,
+                 tol: float = 0.0, resid_tol: float = 0.0, refine_steps: int = -1,
+                 use_graph: bool = True, kappa_max: float = 0.0):
+        lib = load_library()
+        self._lib = lib
+        torch = _torch()
+        keep = []
+        if isinstance(rowptr, torch.Tensor):
+            rp = rowptr.to(torch.int32).contiguous()
+            ci = colind.to(device=rp.device, dtype=torch.int32).contiguous()
+            on_dev = 1 if rp.is_cuda else 0
+            keep += [rp, ci]
+            rp_ptr, ci_ptr = rp.data_ptr(), ci.data_ptr()
+            n, nnz = rp.numel() - 1, ci.numel()
+        else:
+            rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+            ci = np.ascontiguousarray(colind, dtype=np.int32)
+            keep += [rp, ci]
+            on_dev = 0
+            rp_ptr, ci_ptr = rp.ctypes.data, ci.ctypes.data
+            n, nnz = rp.shape[0] - 1, ci.shape[0]
+        csr = CSR(n, nnz, rp_ptr, ci_ptr if nnz > 0 else None, on_dev)
+        o = Opts()
+        lib.submat_default_opts(ctypes.byref(o))
+        o.precision = {"mixed": PREC_MIXED_F16, "fp64": PREC_FP64}[precision]
+        o.k_max = k_max
+        o.tol = tol
+        o.resid_tol = resid_tol
+        o.refine_steps = refine_steps
+        o.use_graph = 1 if use_graph else 0
+        o.kappa_max = kappa_max
+        h = ctypes.c_void_p()
+        _check(lib, lib.submat_plan(ctypes.byref(csr), int(p), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.n = int(n)
+        self.nnz = int(nnz)
+        self.p = int(p)
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.submat_plan_destroy(h)
+            self._h = None
+
+    def rows(self):
+        """(m, pos) as computed on the device: m_j = |R_j|, pos_j = R_j.indexof(j)."""
+        m = np.zeros(self.n, dtype=np.int32)
+        pos = np.zeros(self.n, dtype=np.int32)
+        _check(self._lib, self._lib.submat_plan_rows(self._h, m.ctypes.data, pos.ctypes.data))
+        return m, pos
+
+    def report(self) -> dict:
+        r = Report()
+        _check(self._lib, self._lib.submat_get_report(self._h, ctypes.byref(r)))
+        return r.as_dict()
+
+    def _vals(self, t):
+        torch = _torch()
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+            raise TypeError("expected a CUDA float64 tensor")
+        if t.numel() != self.nnz:
+            raise ValueError(f"expected {self.nnz} values, got {t.numel()}")
+        return t.contiguous()
+
+    def invroot(self, vals, out=None, stream=None, sync: bool = False):
+        torch = _torch()
+        v = self._vals(vals)
+        if out is None:
+            out = torch.empty_like(v)
+        _check(self._lib, self._lib.submat_invroot(self._h, ctypes.c_void_p(v.data_ptr()),
+                                                   ctypes.c_void_p(out.data_ptr()),
+                                                   _stream_ptr(stream), 1 if sync else 0))
+        return out
+
+    def invroot_host(self, vals_in, vals_out=None, stream=None):
+        """Forward on host arrays (numpy float64 or CPU tensors, pinned for async copies)."""
+        torch = _torch()
+        if isinstance(vals_in, torch.Tensor):
+            src = vals_in.contiguous()
+            ptr_in = src.data_ptr()
+        else:
+            src = np.ascontiguousarray(vals_in, dtype=np.float64)
+            ptr_in = src.ctypes.data
+        if vals_out is None:
+            vals_out = np.empty(self.nnz, dtype=np.float64)
+        ptr_out = vals_out.data_ptr() if isinstance(vals_out, torch.Tensor) \
+            else vals_out.ctypes.data
+        _check(self._lib, self._lib.submat_invroot_host(self._h, ctypes.c_void_p(ptr_in),
+                                                        ctypes.c_void_p(ptr_out),
+                                                        _stream_ptr(stream)))
+        return vals_out
+
+    def backward(self, grad_out, grad_in=None, stream=None):
+        torch = _torch()
+        g = self._vals(grad_out)
+        if grad_in is None:
+            grad_in = torch.empty_like(g)
+        _check(self._lib, self._lib.submat_invroot_backward(
+            self._h, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(grad_in.data_ptr()),
+            _stream_ptr(stream)))
+        return grad_in
+
+
+def submat_plan(rowptr, colind, p: int, **kw) -> Plan:
+    """``submat_plan``: validate A's pattern and build the integer plan (Alg. 1)."""
+    return Plan(rowptr, colind, p, **kw)
+
+
+def submat_invroot(plan: Plan, vals_in, vals_out=None, stream=None, sync: bool = False):
+    """``submat_invroot``: the submatrix method's A^(-1/p) on A's pattern."""
+    return plan.invroot(vals_in, vals_out, stream, sync)
+
+
+def submat_invroot_backward(plan: Plan, grad_out, grad_in=None, stream=None):
+    """``submat_invroot_backward``: gradient w.r.t. A's stored values (last forward)."""
+    return plan.backward(grad_out, grad_in, stream)
+
+
+def _make_function():
+    torch = _torch()
+
+    class SubmatInvRoot(torch.autograd.Function):
+        """Autograd wrapper: forward = submat_invroot, backward = submat_invroot_backward.
+
+        The plan keeps the forward input, so nothing is saved on the tape."""
+
+        @staticmethod
+        def forward(ctx, vals, plan):
+            ctx.plan = plan
+            return plan.invroot(vals)
+
+        @staticmethod
+        def backward(ctx, grad):
+            return ctx.plan.backward(grad.contiguous()), None
+
+    return SubmatInvRoot
+
+
+def __getattr__(name):
+    if name == "SubmatInvRoot":
+        f = _make_function()
+        globals()["SubmatInvRoot"] = f
+        return f
+    raise AttributeError(name)

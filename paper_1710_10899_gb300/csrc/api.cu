@@ -1,0 +1,474 @@
+// C ABI of libsubmat.so (declared in include/submat.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace submat {
+cudaError_t set_attr_mixed();
+cudaError_t set_attr_fp64();
+cudaError_t set_attr_eig();
+}  // namespace submat
+
+using namespace submat;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+submat_status fail(submat_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                  \
+  do {                                                                                  \
+    cudaError_t err_ = (expr);                                                          \
+    if (err_ != cudaSuccess) {                                                          \
+      return fail(err_ == cudaErrorMemoryAllocation ? SUBMAT_ENOMEM : SUBMAT_ECUDA,     \
+                  std::string(#expr) + ": " + cudaGetErrorString(err_));                \
+    }                                                                                   \
+  } while (0)
+
+struct GraphEntry {
+  const double* in = nullptr;
+  double* out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct submat_plan_s {
+  int device = 0;
+  int n_sm = 0;
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int32_t p = 1;
+  submat_opts opts{};
+  int32_t* d_rowptr = nullptr;
+  int32_t* d_colind = nullptr;
+  int32_t* d_m = nullptr;
+  int32_t* d_pos = nullptr;
+  int32_t* d_order = nullptr;
+  int32_t* d_fallback = nullptr;
+  int32_t* d_flags = nullptr;
+  DevCounters* d_ctr = nullptr;       // forward counters
+  DevCounters* d_ctr_bwd = nullptr;   // backward counters
+  char* d_scratch = nullptr;
+  size_t stride = 0;
+  int grid = 0;
+  double* d_saved = nullptr;
+  bool have_fwd = false;
+  int32_t m_max = 0;
+  double sum_m3 = 0.0;
+  cudaStream_t last_stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  double* d_host_in = nullptr;     // device staging of submat_invroot_host
+  double* d_host_out = nullptr;
+  std::vector<GraphEntry> graphs;
+};
+
+namespace {
+
+void release(submat_plan_t P) {
+  if (!P) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(P->device);
+  for (auto& g : P->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+  for (auto& e : P->ev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(P->d_host_in);
+  cudaFree(P->d_host_out);
+  cudaFree(P->d_rowptr);
+  cudaFree(P->d_colind);
+  cudaFree(P->d_m);
+  cudaFree(P->d_pos);
+  cudaFree(P->d_order);
+  cudaFree(P->d_fallback);
+  cudaFree(P->d_flags);
+  cudaFree(P->d_ctr);
+  cudaFree(P->d_ctr_bwd);
+  cudaFree(P->d_scratch);
+  cudaFree(P->d_saved);
+  cudaSetDevice(prev);
+  delete P;
+}
+
+// Queue the forward of plan P on stream s.
+submat_status enqueue_forward(submat_plan_t P, const double* in, double* out, cudaStream_t s,
+                              bool capturing) {
+  const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  FwdArgs a{};
+  a.rowptr = P->d_rowptr;
+  a.colind = P->d_colind;
+  a.m = P->d_m;
+  a.pos = P->d_pos;
+  a.order = P->d_order;
+  a.n = P->n;
+  a.p = P->p;
+  a.vals_in = in;
+  a.vals_out = out;
+  a.ctr = P->d_ctr;
+  a.fallback_list = P->d_fallback;
+  a.scratch = P->d_scratch;
+  a.scratch_stride = P->stride;
+  a.k_max = P->opts.k_max;
+  a.tol = P->opts.tol;
+  a.resid_tol = P->opts.resid_tol;
+  a.refine_steps = P->opts.refine_steps;
+  a.kappa_max = P->opts.kappa_max;
+  CUDA_TRY(cudaMemcpyAsync(P->d_saved, in, (size_t)P->nnz * sizeof(double),
+                           cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(P->d_ctr, 0, sizeof(DevCounters), s));
+  CUDA_TRY(cudaEventRecordWithFlags(P->ev[0], s, evf));
+  if (P->opts.precision == SUBMAT_PREC_FP64)
+    CUDA_TRY(launch_fwd_fp64(a, P->grid, s));
+  else
+    CUDA_TRY(launch_fwd_mixed(a, P->grid, s));
+  CUDA_TRY(cudaEventRecordWithFlags(P->ev[1], s, evf));
+  CUDA_TRY(launch_fallback(a, P->grid, s));
+  CUDA_TRY(cudaEventRecordWithFlags(P->ev[2], s, evf));
+  return SUBMAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void submat_default_opts(submat_opts* o) {
+  if (!o) return;
+  o->precision = SUBMAT_PREC_MIXED_F16;
+  o->k_max = 40;
+  o->tol = 0.0;
+  o->resid_tol = 1e-3;
+  o->refine_steps = -1;
+  o->use_graph = 1;
+  o->kappa_max = 100.0;
+}
+
+const char* submat_status_string(submat_status s) {
+  switch (s) {
+    case SUBMAT_OK: return "ok";
+    case SUBMAT_EINVAL: return "invalid argument";
+    case SUBMAT_ENODIAG: return "diagonal entry not stored";
+    case SUBMAT_ENOTSYM: return "pattern not symmetric";
+    case SUBMAT_ETOOBIG: return "row longer than SUBMAT_MAX_M";
+    case SUBMAT_ENOMEM: return "out of memory";
+    case SUBMAT_ECUDA: return "CUDA error";
+    case SUBMAT_ENOTSPD: return "submatrix not positive definite";
+    case SUBMAT_ENOFWD: return "no forward on this plan";
+  }
+  return "unknown status";
+}
+
+const char* submat_last_error(void) { return g_last_error.c_str(); }
+
+submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* opts,
+                          submat_plan_t* out) {
+  g_last_error.clear();
+  if (!out) return fail(SUBMAT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!csr) return fail(SUBMAT_EINVAL, "csr is NULL");
+  if (p < 1) return fail(SUBMAT_EINVAL, "p must be >= 1");
+  if (csr->n < 0 || csr->nnz < 0) return fail(SUBMAT_EINVAL, "negative size");
+  if (csr->nnz > INT32_MAX) return fail(SUBMAT_EINVAL, "nnz exceeds int32 indexing");
+  if (!csr->rowptr || (csr->nnz > 0 && !csr->colind))
+    return fail(SUBMAT_EINVAL, "NULL rowptr/colind");
+
+  submat_opts o;
+  submat_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.precision != SUBMAT_PREC_FP64 && o.precision != SUBMAT_PREC_MIXED_F16)
+    return fail(SUBMAT_EINVAL, "unknown precision");
+  if (o.k_max < 1) o.k_max = 40;
+  if (!(o.tol > 0.0)) o.tol = (o.precision == SUBMAT_PREC_FP64) ? 1e-7 : 1e-4;
+  if (!(o.resid_tol > 0.0)) o.resid_tol = 1e-3;
+  if (o.refine_steps < 0) o.refine_steps = (p == 1) ? 2 : 0;
+  if (!(o.kappa_max > 0.0)) o.kappa_max = 100.0;
+
+  const int32_t n = csr->n;
+  const int64_t nnz = csr->nnz;
+  std::vector<int32_t> h_rowptr(n + 1);
+  if (csr->on_device) {
+    CUDA_TRY(cudaMemcpy(h_rowptr.data(), csr->rowptr, (n + 1) * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(h_rowptr.data(), csr->rowptr, (n + 1) * sizeof(int32_t));
+  }
+  if (h_rowptr[0] != 0 || h_rowptr[n] != nnz)
+    return fail(SUBMAT_EINVAL, "rowptr[0] must be 0 and rowptr[n] must be nnz");
+  int32_t m_max = 0;
+  double sum_m3 = 0.0;
+  for (int32_t j = 0; j < n; ++j) {
+    const int32_t len = h_rowptr[j + 1] - h_rowptr[j];
+    if (len < 0) return fail(SUBMAT_EINVAL, "rowptr not nondecreasing");
+    if (len == 0) return fail(SUBMAT_ENODIAG, "empty row " + std::to_string(j));
+    if (len > SUBMAT_MAX_M)
+      return fail(SUBMAT_ETOOBIG, "row " + std::to_string(j) + " has " + std::to_string(len) +
+                                      " entries (max " + std::to_string(SUBMAT_MAX_M) + ")");
+    m_max = std::max(m_max, len);
+    sum_m3 += (double)len * len * len;
+  }
+
+  submat_plan_t P = new (std::nothrow) submat_plan_s();
+  if (!P) return fail(SUBMAT_ENOMEM, "host allocation");
+  P->n = n;
+  P->nnz = nnz;
+  P->p = p;
+  P->opts = o;
+  P->m_max = m_max;
+  P->sum_m3 = sum_m3;
+  auto bail = [&](submat_status st) {
+    release(P);
+    return st;
+  };
+#define PLAN_TRY(expr)                                                              \
+  do {                                                                              \
+    cudaError_t err_ = (expr);                                                      \
+    if (err_ != cudaSuccess) {                                                      \
+      fail(err_ == cudaErrorMemoryAllocation ? SUBMAT_ENOMEM : SUBMAT_ECUDA,        \
+           std::string(#expr) + ": " + cudaGetErrorString(err_));                   \
+      return bail(err_ == cudaErrorMemoryAllocation ? SUBMAT_ENOMEM : SUBMAT_ECUDA); \
+    }                                                                               \
+  } while (0)
+
+  PLAN_TRY(cudaGetDevice(&P->device));
+  PLAN_TRY(cudaDeviceGetAttribute(&P->n_sm, cudaDevAttrMultiProcessorCount, P->device));
+  PLAN_TRY(set_attr_mixed());
+  PLAN_TRY(set_attr_fp64());
+  PLAN_TRY(set_attr_eig());
+  const size_t nb = (size_t)(n > 0 ? n : 1);
+  PLAN_TRY(cudaMalloc(&P->d_rowptr, (n + 1) * sizeof(int32_t)));
+  PLAN_TRY(cudaMalloc(&P->d_colind, (nnz > 0 ? nnz : 1) * sizeof(int32_t)));
+  PLAN_TRY(cudaMalloc(&P->d_m, nb * sizeof(int32_t)));
+  PLAN_TRY(cudaMalloc(&P->d_pos, nb * sizeof(int32_t)));
+  PLAN_TRY(cudaMalloc(&P->d_order, nb * sizeof(int32_t)));
+  PLAN_TRY(cudaMalloc(&P->d_fallback, nb * sizeof(int32_t)));
+  PLAN_TRY(cudaMalloc(&P->d_flags, sizeof(int32_t)));
+  PLAN_TRY(cudaMalloc(&P->d_ctr, sizeof(DevCounters)));
+  PLAN_TRY(cudaMalloc(&P->d_ctr_bwd, sizeof(DevCounters)));
+  PLAN_TRY(cudaMemset(P->d_ctr, 0, sizeof(DevCounters)));
+  PLAN_TRY(cudaMemset(P->d_ctr_bwd, 0, sizeof(DevCounters)));
+  PLAN_TRY(cudaMemcpy(P->d_rowptr, h_rowptr.data(), (n + 1) * sizeof(int32_t),
+                      cudaMemcpyHostToDevice));
+  if (nnz > 0)
+    PLAN_TRY(cudaMemcpy(P->d_colind, csr->colind, nnz * sizeof(int32_t),
+                        csr->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  PLAN_TRY(cudaMemset(P->d_flags, 0, sizeof(int32_t)));
+  PLAN_TRY(launch_check_pattern(P->d_rowptr, P->d_colind, n, P->d_flags, 0));
+  int32_t flags = 0;
+  PLAN_TRY(cudaMemcpy(&flags, P->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (flags & 1) { fail(SUBMAT_EINVAL, "column index out of range"); return bail(SUBMAT_EINVAL); }
+  if (flags & 2) {
+    fail(SUBMAT_EINVAL, "column indices not strictly ascending within a row");
+    return bail(SUBMAT_EINVAL);
+  }
+  if (flags & 4) { fail(SUBMAT_ENOTSYM, "pattern not symmetric"); return bail(SUBMAT_ENOTSYM); }
+  PLAN_TRY(launch_plan_rows(P->d_rowptr, P->d_colind, n, P->d_m, P->d_pos, P->d_flags, 0));
+  PLAN_TRY(cudaMemcpy(&flags, P->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (flags & 8) {
+    fail(SUBMAT_ENODIAG, "a row does not store its diagonal entry");
+    return bail(SUBMAT_ENODIAG);
+  }
+  // Rows by decreasing size (longest first), ties by index: counting sort on m.
+  std::vector<int32_t> h_m(nb), order(nb);
+  if (n > 0) PLAN_TRY(cudaMemcpy(h_m.data(), P->d_m, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  {
+    std::vector<int64_t> start(SUBMAT_MAX_M + 2, 0);
+    for (int32_t j = 0; j < n; ++j) start[SUBMAT_MAX_M - h_m[j]]++;
+    int64_t acc = 0;
+    for (auto& v : start) { const int64_t c = v; v = acc; acc += c; }
+    for (int32_t j = 0; j < n; ++j) order[start[SUBMAT_MAX_M - h_m[j]]++] = j;
+  }
+  if (n > 0)
+    PLAN_TRY(cudaMemcpy(P->d_order, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+
+  const int mp = std::max(pad_mixed(m_max), pad_fp64(m_max));
+  size_t stride = std::max(scratch_eig(mp), o.precision == SUBMAT_PREC_FP64 ? scratch_fp64(mp)
+                                                                             : scratch_mixed(mp));
+  stride = (stride + 1023) / 1024 * 1024;
+  P->stride = stride;
+  P->grid = std::max(1, std::min(P->n_sm, n));
+  PLAN_TRY(cudaMalloc(&P->d_scratch, stride * (size_t)P->grid));
+  PLAN_TRY(cudaMalloc(&P->d_saved, (nnz > 0 ? nnz : 1) * sizeof(double)));
+  PLAN_TRY(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  for (auto& e : P->ev) PLAN_TRY(cudaEventCreate(&e));
+  PLAN_TRY(cudaDeviceSynchronize());
+#undef PLAN_TRY
+  *out = P;
+  return SUBMAT_OK;
+}
+
+submat_status submat_invroot(submat_plan_t P, const double* in, double* out, void* stream,
+                             int32_t sync) {
+  g_last_error.clear();
+  if (!P) return fail(SUBMAT_EINVAL, "plan is NULL");
+  if (P->n == 0) return SUBMAT_OK;
+  if (!in || !out) return fail(SUBMAT_EINVAL, "NULL value array");
+  const char* a0 = reinterpret_cast<const char*>(in);
+  const char* b0 = reinterpret_cast<const char*>(out);
+  const size_t bytes = (size_t)P->nnz * sizeof(double);
+  if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(SUBMAT_EINVAL, "vals_out overlaps vals_in");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int prev = 0;
+  CUDA_TRY(cudaGetDevice(&prev));
+  if (prev != P->device) CUDA_TRY(cudaSetDevice(P->device));
+  submat_status st = SUBMAT_OK;
+  if (P->opts.use_graph) {
+    GraphEntry* ge = nullptr;
+    for (auto& g : P->graphs)
+      if (g.in == in && g.out == out) ge = &g;
+    if (!ge) {
+      if (P->graphs.size() >= 8) {
+        cudaGraphExecDestroy(P->graphs.front().exec);
+        P->graphs.erase(P->graphs.begin());
+      }
+      cudaGraph_t graph = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
+      st = enqueue_forward(P, in, out, P->cap_stream, true);
+      cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &graph);
+      if (st != SUBMAT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      CUDA_TRY(ce);
+      GraphEntry g;
+      g.in = in;
+      g.out = out;
+      cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CUDA_TRY(ie);
+      P->graphs.push_back(g);
+      ge = &P->graphs.back();
+    }
+    CUDA_TRY(cudaGraphLaunch(ge->exec, s));
+  } else {
+    st = enqueue_forward(P, in, out, s, false);
+    if (st != SUBMAT_OK) return st;
+  }
+  P->last_stream = s;
+  P->have_fwd = true;
+  if (sync) {
+    CUDA_TRY(cudaStreamSynchronize(s));
+    DevCounters c;
+    CUDA_TRY(cudaMemcpy(&c, P->d_ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    if (c.n_notspd > 0)
+      return fail(SUBMAT_ENOTSPD, std::to_string(c.n_notspd) + " submatrices not SPD");
+  }
+  if (prev != P->device) CUDA_TRY(cudaSetDevice(prev));
+  return SUBMAT_OK;
+}
+
+submat_status submat_invroot_host(submat_plan_t P, const double* in, double* out, void* stream) {
+  g_last_error.clear();
+  if (!P) return fail(SUBMAT_EINVAL, "plan is NULL");
+  if (P->n == 0) return SUBMAT_OK;
+  if (!in || !out) return fail(SUBMAT_EINVAL, "NULL value array");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)P->nnz * sizeof(double);
+  if (!P->d_host_in) {
+    CUDA_TRY(cudaMalloc(&P->d_host_in, bytes));
+    CUDA_TRY(cudaMalloc(&P->d_host_out, bytes));
+  }
+  CUDA_TRY(cudaMemcpyAsync(P->d_host_in, in, bytes, cudaMemcpyHostToDevice, s));
+  submat_status st = submat_invroot(P, P->d_host_in, P->d_host_out, stream, 0);
+  if (st != SUBMAT_OK) return st;
+  CUDA_TRY(cudaMemcpyAsync(out, P->d_host_out, bytes, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  DevCounters c;
+  CUDA_TRY(cudaMemcpy(&c, P->d_ctr, sizeof(c), cudaMemcpyDeviceToHost));
+  if (c.n_notspd > 0)
+    return fail(SUBMAT_ENOTSPD, std::to_string(c.n_notspd) + " submatrices not SPD");
+  return SUBMAT_OK;
+}
+
+submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, double* grad_in,
+                                      void* stream) {
+  g_last_error.clear();
+  if (!P) return fail(SUBMAT_EINVAL, "plan is NULL");
+  if (!P->have_fwd) return fail(SUBMAT_ENOFWD, "backward before forward");
+  if (P->n == 0) return SUBMAT_OK;
+  if (!grad_out || !grad_in) return fail(SUBMAT_EINVAL, "NULL gradient array");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int prev = 0;
+  CUDA_TRY(cudaGetDevice(&prev));
+  if (prev != P->device) CUDA_TRY(cudaSetDevice(P->device));
+  BwdArgs a{};
+  a.rowptr = P->d_rowptr;
+  a.colind = P->d_colind;
+  a.m = P->d_m;
+  a.pos = P->d_pos;
+  a.order = P->d_order;
+  a.n = P->n;
+  a.p = P->p;
+  a.vals = P->d_saved;
+  a.grad_out = grad_out;
+  a.grad_in = grad_in;
+  a.ctr = P->d_ctr_bwd;
+  a.scratch = P->d_scratch;
+  a.scratch_stride = P->stride;
+  CUDA_TRY(cudaMemsetAsync(grad_in, 0, (size_t)P->nnz * sizeof(double), s));
+  CUDA_TRY(cudaMemsetAsync(P->d_ctr_bwd, 0, sizeof(DevCounters), s));
+  CUDA_TRY(launch_backward(a, P->grid, s));
+  P->last_stream = s;
+  if (prev != P->device) CUDA_TRY(cudaSetDevice(prev));
+  return SUBMAT_OK;
+}
+
+submat_status submat_get_report(submat_plan_t P, submat_report* r) {
+  g_last_error.clear();
+  if (!P || !r) return fail(SUBMAT_EINVAL, "NULL argument");
+  std::memset(r, 0, sizeof(*r));
+  r->n_rows = P->n;
+  r->m_max = P->m_max;
+  r->sum_m3 = P->sum_m3;
+  if (P->n == 0) return SUBMAT_OK;
+  CUDA_TRY(cudaStreamSynchronize(P->last_stream));
+  DevCounters c;
+  CUDA_TRY(cudaMemcpy(&c, P->d_ctr, sizeof(c), cudaMemcpyDeviceToHost));
+  r->iters_max = c.iters_max;
+  r->iters_sum = (int64_t)c.iters_sum;
+  r->n_fallback = c.n_fallback;
+  r->n_notspd = (int64_t)c.n_notspd;
+  double mr;
+  unsigned long long bits = c.resid_max_bits;
+  std::memcpy(&mr, &bits, sizeof(mr));
+  r->max_resid = mr;
+  r->flops_tensor = c.flops_tensor;
+  r->flops_fp64 = c.flops_fp64;
+  r->n_illcond = (int64_t)c.n_illcond;
+  if (P->have_fwd) {
+    CUDA_TRY(cudaEventElapsedTime(&r->ms_kernel, P->ev[0], P->ev[1]));
+    CUDA_TRY(cudaEventElapsedTime(&r->ms_fallback, P->ev[1], P->ev[2]));
+  }
+  return SUBMAT_OK;
+}
+
+submat_status submat_plan_rows(submat_plan_t P, int32_t* m, int32_t* pos) {
+  g_last_error.clear();
+  if (!P || (P->n > 0 && (!m || !pos))) return fail(SUBMAT_EINVAL, "NULL argument");
+  if (P->n == 0) return SUBMAT_OK;
+  CUDA_TRY(cudaMemcpy(m, P->d_m, P->n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(pos, P->d_pos, P->n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return SUBMAT_OK;
+}
+
+submat_status submat_plan_shape(submat_plan_t P, int32_t* n, int64_t* nnz) {
+  if (!P) return fail(SUBMAT_EINVAL, "plan is NULL");
+  if (n) *n = P->n;
+  if (nnz) *nnz = P->nnz;
+  return SUBMAT_OK;
+}
+
+void submat_plan_destroy(submat_plan_t P) { release(P); }
+
+}  // extern "C"

@@ -1,0 +1,269 @@
+// FP64 symmetric eigendecomposition of one submatrix per CTA (cyclic Jacobi, round-robin
+// ordering so that m/2 disjoint rotations run in parallel), and the two kernels built on it:
+//
+//   fallback: rows whose mixed/FP64 Newton result failed its residual test are recomputed
+//             from S = V diag(lambda) V^T as column pos of V diag(lambda^(-1/p)) V^T;
+//             a non-positive (or non-finite) eigenvalue marks the row NaN (not SPD).
+//   backward: the Daleckii-Krein adjoint (Higham, Functions of Matrices, Thm. 3.11):
+//             for L = <g, column pos of f(S)>, f(x) = x^(-1/p), and the symmetrised
+//             cotangent Gbar = (g e_pos^T + e_pos g^T)/2,
+//             dL/dS = V (Gamma o (V^T Gbar V)) V^T,  Gamma_ab = divided difference of f,
+//             with V^T Gbar V = (u w^T + w u^T)/2, u = V^T g, w = V^T e_pos; the result is
+//             added into the gradient of every stored entry (R[k], R[l]).
+//
+// Rotation: the symmetric 2x2 Schur decomposition of Golub & Van Loan (Alg. 8.4.1).
+#include "common.cuh"
+
+namespace submat {
+namespace {
+
+constexpr int kMaxSweeps = 30;
+
+// Eigendecomposition of the symmetric m x m matrix A (ld m, global) in place: on return
+// A's diagonal holds the eigenvalues and V (ld m) the eigenvectors (columns).
+// pair_s: 2*ceil(m/2) ints, cs_s: 2*ceil(m/2) doubles (shared).  Returns the sweeps used,
+// or -1 if A holds a non-finite value (nothing is decomposed then).
+__device__ int jacobi_eig(double* __restrict__ A, double* __restrict__ V, int m, int* pair_s,
+                          double* cs_s, double* red_s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < m * m; e += blockDim.x) V[e] = (e / m == e % m) ? 1.0 : 0.0;
+  __syncthreads();
+  const int mm = m + (m & 1);
+  const int np = mm / 2;
+  int sweep = 0;
+  for (; sweep < kMaxSweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const double v = A[e];
+      tot += v * v;
+      if (e / m != e % m) off += v * v;
+    }
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if (lane == 0) { red_s[warp] = off; red_s[kWarps + warp] = tot; }
+    __syncthreads();
+    double so = 0.0, st = 0.0;
+    for (int w = 0; w < kWarps; ++w) { so += red_s[w]; st += red_s[kWarps + w]; }
+    __syncthreads();
+    if (!(st <= 1.7e308)) return -1;     // NaN or infinity somewhere in A
+    if (m == 1 || !(so > 1e-28 * st)) break;       // off(A) <= 1e-14 ||A||_F
+    for (int s = 0; s < mm - 1; ++s) {
+      for (int k = tid; k < np; k += blockDim.x) {
+        int p, q;
+        if (k == 0) { p = s; q = mm - 1; }
+        else { p = (s + k) % (mm - 1); q = (s - k + mm - 1) % (mm - 1); }
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, sn = 0.0;
+        if (q < m) {
+          const double apq = A[p * m + q];
+          if (apq != 0.0) {
+            const double tau = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        }
+        pair_s[2 * k] = p; pair_s[2 * k + 1] = q;
+        cs_s[2 * k] = c; cs_s[2 * k + 1] = sn;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int e = tid; e < np * m; e += blockDim.x) {
+        const int k = e / m, i = e % m;
+        const int p = pair_s[2 * k], q = pair_s[2 * k + 1];
+        if (q >= m) continue;
+        const double c = cs_s[2 * k], sn = cs_s[2 * k + 1];
+        if (sn == 0.0) continue;
+        const double ap = A[i * m + p], aq = A[i * m + q];
+        A[i * m + p] = c * ap - sn * aq;
+        A[i * m + q] = sn * ap + c * aq;
+        const double vp = V[i * m + p], vq = V[i * m + q];
+        V[i * m + p] = c * vp - sn * vq;
+        V[i * m + q] = sn * vp + c * vq;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = tid; e < np * m; e += blockDim.x) {
+        const int k = e / m, i = e % m;
+        const int p = pair_s[2 * k], q = pair_s[2 * k + 1];
+        if (q >= m) continue;
+        const double c = cs_s[2 * k], sn = cs_s[2 * k + 1];
+        if (sn == 0.0) continue;
+        const double ap = A[p * m + i], aq = A[q * m + i];
+        A[p * m + i] = c * ap - sn * aq;
+        A[q * m + i] = sn * ap + c * aq;
+      }
+      __syncthreads();
+    }
+  }
+  return sweep;
+}
+
+__device__ void gather_dense(const int32_t* rowptr, const int32_t* colind, const double* vals,
+                             int j, int m, int32_t* R_s, double* S, double* red_s) {
+  (void)gather_submatrix(rowptr, colind, vals, j, m, R_s, S, red_s);
+}
+
+__global__ void __launch_bounds__(kThreads) fallback_kernel(FwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* cs_s = reinterpret_cast<double*>(smem_raw);               // SUBMAT_MAX_M
+  double* lam_s = cs_s + SUBMAT_MAX_M;                                // SUBMAT_MAX_M
+  double* red_s = lam_s + SUBMAT_MAX_M;                               // 2*kWarps
+  int32_t* pair_s = reinterpret_cast<int32_t*>(red_s + 2 * kWarps);  // SUBMAT_MAX_M
+  int32_t* R_s = pair_s + SUBMAT_MAX_M;                               // SUBMAT_MAX_M
+  __shared__ int job_s;
+  __shared__ int bad_s;
+  char* scr = a.scratch + (size_t)blockIdx.x * a.scratch_stride;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) job_s = atomicAdd(&a.ctr->fb_queue, 1);
+    __syncthreads();
+    const int idx = job_s;
+    __syncthreads();
+    if (idx >= a.ctr->n_fallback) break;
+    const int j = a.fallback_list[idx];
+    const int m = a.m[j], pos = a.pos[j], p = a.p;
+    double* A = reinterpret_cast<double*>(scr);
+    double* V = A + (size_t)m * m;
+    gather_dense(a.rowptr, a.colind, a.vals_in, j, m, R_s, A, red_s);
+    const int sweeps = jacobi_eig(A, V, m, pair_s, cs_s, red_s);
+    if (tid == 0) bad_s = sweeps < 0 ? 1 : 0;
+    __syncthreads();
+    for (int i = tid; i < m; i += blockDim.x) {
+      const double l = A[i * m + i];
+      if (!(l > 0.0) || !(l < 1e308)) bad_s = 1;
+      lam_s[i] = pow(l, -1.0 / (double)p) * V[pos * m + i];
+    }
+    __syncthreads();
+    double* out = a.vals_out + a.rowptr[j];
+    const bool bad = bad_s != 0;
+    for (int k = tid; k < m; k += blockDim.x) {
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s = fma(V[k * m + i], lam_s[i], s);
+      out[k] = bad ? __longlong_as_double(0x7ff8000000000000ll) : s;
+    }
+    if (tid == 0 && bad) atomicAdd(&a.ctr->n_notspd, 1ull);
+    if (tid == 0) atomicAdd(&a.ctr->flops_fp64, 12.0 * (double)m * m * m + 2.0 * m * m);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* cs_s = reinterpret_cast<double*>(smem_raw);               // SUBMAT_MAX_M
+  double* al_s = cs_s + SUBMAT_MAX_M;                                 // alpha = lambda^(1/p)
+  double* u_s = al_s + SUBMAT_MAX_M;                                  // V^T g
+  double* w_s = u_s + SUBMAT_MAX_M;                                   // V^T e_pos
+  double* red_s = w_s + SUBMAT_MAX_M;                                 // 2*kWarps
+  int32_t* pair_s = reinterpret_cast<int32_t*>(red_s + 2 * kWarps);  // SUBMAT_MAX_M
+  int32_t* R_s = pair_s + SUBMAT_MAX_M;                               // SUBMAT_MAX_M
+  __shared__ int job_s;
+  __shared__ int bad_s;
+  char* scr = a.scratch + (size_t)blockIdx.x * a.scratch_stride;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (;;) {
+    if (tid == 0) job_s = atomicAdd(&a.ctr->queue, 1);
+    __syncthreads();
+    const int idx = job_s;
+    __syncthreads();
+    if (idx >= a.n) break;
+    const int j = a.order[idx];
+    const int m = a.m[j], pos = a.pos[j], p = a.p;
+    double* A = reinterpret_cast<double*>(scr);
+    double* V = A + (size_t)m * m;
+    double* W = V + (size_t)m * m;
+    gather_dense(a.rowptr, a.colind, a.vals, j, m, R_s, A, red_s);
+    const int sweeps = jacobi_eig(A, V, m, pair_s, cs_s, red_s);
+    if (tid == 0) bad_s = sweeps < 0 ? 1 : 0;
+    __syncthreads();
+    const double* g = a.grad_out + a.rowptr[j];
+    for (int i = tid; i < m; i += blockDim.x) {
+      const double l = A[i * m + i];
+      if (!(l > 0.0) || !(l < 1e308)) bad_s = 1;
+      al_s[i] = pow(l, 1.0 / (double)p);
+      w_s[i] = V[pos * m + i];
+    }
+    // u = V^T g: one warp per component
+    for (int i = warp; i < m; i += kWarps) {
+      double s = 0.0;
+      for (int k = lane; k < m; k += 32) s = fma(V[k * m + i], g[k], s);
+      s = warp_sum(s);
+      if (lane == 0) u_s[i] = s;
+    }
+    __syncthreads();
+    if (bad_s) {
+      if (tid == 0) atomicAdd(&a.ctr->n_notspd, 1ull);
+      __syncthreads();
+      continue;
+    }
+    // Q_ab = Gamma_ab (u_a w_b + w_a u_b) / 2, stored in A (the eigenvalues are in al_s)
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int x = e / m, y = e % m;
+      const double ax = al_s[x], ay = al_s[y];
+      double ssum = 0.0, px = 1.0;
+      for (int i = 0; i < p; ++i) {
+        double py = 1.0;
+        for (int t = 0; t < p - 1 - i; ++t) py *= ay;
+        ssum += px * py;
+        px *= ax;
+      }
+      const double gam = -1.0 / (ax * ay * ssum);
+      A[e] = gam * 0.5 * (u_s[x] * w_s[y] + w_s[x] * u_s[y]);
+    }
+    __syncthreads();
+    // W = V Q
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int x = e / m, y = e % m;
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s = fma(V[x * m + k], A[k * m + y], s);
+      W[e] = s;
+    }
+    __syncthreads();
+    // G = W V^T, written over A
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int x = e / m, y = e % m;
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s = fma(W[x * m + k], V[y * m + k], s);
+      A[e] = s;
+    }
+    __syncthreads();
+    // scatter-add G[k][l] into the stored entry (R[k], R[l])
+    for (int k = warp; k < m; k += kWarps) {
+      const int r = R_s[k];
+      for (int e = a.rowptr[r] + lane; e < a.rowptr[r + 1]; e += 32) {
+        const int l = find_sorted(R_s, m, a.colind[e]);
+        if (l >= 0) atomicAdd(a.grad_in + e, A[k * m + l]);
+      }
+    }
+    if (tid == 0) atomicAdd(&a.ctr->flops_fp64, 16.0 * (double)m * m * m);
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+size_t smem_fallback() {
+  return (2 * SUBMAT_MAX_M + 2 * kWarps) * sizeof(double) + 2 * SUBMAT_MAX_M * sizeof(int32_t);
+}
+size_t smem_backward() {
+  return (4 * SUBMAT_MAX_M + 2 * kWarps) * sizeof(double) + 2 * SUBMAT_MAX_M * sizeof(int32_t);
+}
+size_t scratch_eig(int mp) { return 3 * (size_t)mp * mp * sizeof(double); }
+
+cudaError_t launch_fallback(const FwdArgs& a, int grid, cudaStream_t s) {
+  fallback_kernel<<<grid, kThreads, smem_fallback(), s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_backward(const BwdArgs& a, int grid, cudaStream_t s) {
+  backward_kernel<<<grid, kThreads, smem_backward(), s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t set_attr_eig() {
+  cudaError_t e = cudaFuncSetAttribute(fallback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_fallback());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_backward());
+}
+
+}  // namespace submat

@@ -1,0 +1,66 @@
+"""C ABI checks that need no GPU: the library builds and loads, exports every function
+that include/submat.h declares, and rejects bad patterns on the host before any CUDA call."""
+import ctypes
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1710_10899_gb300 as pkg
+    if not os.path.exists(pkg.LIB_PATH):
+        if shutil.which("nvcc") is None:
+            pytest.skip("libsubmat.so not built and nvcc not available")
+        from paper_1710_10899_gb300 import build
+        build.build()
+    return pkg.load_library()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "submat.h")).read()
+    return sorted(set(re.findall(r"SUBMAT_API\s+[\w\s\*]+?\b(submat_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    import paper_1710_10899_gb300 as pkg
+    assert sorted(pkg.EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_and_defaults(lib):
+    import paper_1710_10899_gb300 as pkg
+    for code in pkg.STATUS:
+        assert lib.submat_status_string(code)
+    o = pkg.Opts()
+    lib.submat_default_opts(ctypes.byref(o))
+    assert o.precision == pkg.PREC_MIXED_F16 and o.k_max == 40 and o.use_graph == 1
+
+
+def _plan_status(lib, rowptr, colind, p=2):
+    import paper_1710_10899_gb300 as pkg
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    csr = pkg.CSR(len(rp) - 1, len(ci), rp.ctypes.data, ci.ctypes.data if len(ci) else None, 0)
+    h = ctypes.c_void_p()
+    st = lib.submat_plan(ctypes.byref(csr), p, None, ctypes.byref(h))
+    return pkg.STATUS[st]
+
+
+def test_host_side_validation(lib):
+    # these are rejected before the library touches the GPU
+    assert _plan_status(lib, [0, 1], [0], p=0) == "SUBMAT_EINVAL"
+    assert _plan_status(lib, [1, 1], [0]) == "SUBMAT_EINVAL"            # rowptr[0] != 0
+    assert _plan_status(lib, [0, 2, 1], [0, 1]) == "SUBMAT_EINVAL"      # decreasing rowptr
+    assert _plan_status(lib, [0, 1, 1], [0]) == "SUBMAT_ENODIAG"        # empty row
+    big = 1537
+    assert _plan_status(lib, [0, big], np.arange(big)) == "SUBMAT_ETOOBIG"
+    assert lib.submat_plan(None, 2, None, None) != 0

@@ -1,0 +1,55 @@
+"""The Daleckii-Krein adjoint on the GPU against the FP64 oracle gradient and against
+central finite differences of the GPU forward (FP64 path)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1710_10899_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_grad_matches_oracle(sm, p):
+    a = wl.overlap_uniform(n=500, kappa=1e3)
+    w = wl.random_on_pattern(a, seed=1)
+    plan = sm.submat_plan(a.rowptr, a.colind, p)
+    v = torch.tensor(a.vals, device="cuda")
+    sm.submat_invroot(plan, v)
+    g = sm.submat_invroot_backward(plan, torch.tensor(w, device="cuda")).cpu().numpy()
+    gref = oracle.grad(a.rowptr, a.colind, a.vals, p, w)
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) <= 1e-10
+    assert np.abs(g - gref).max() <= 1e-10 * np.abs(gref).max()
+
+
+def test_autograd_and_central_differences(sm):
+    a = wl.overlap_grad(n=2048)                 # the differentiation workload, scaled down
+    w = torch.tensor(wl.random_on_pattern(a, seed=1), device="cuda")
+    plan = sm.submat_plan(a.rowptr, a.colind, 2, precision="fp64")
+    vals = torch.tensor(a.vals, device="cuda", requires_grad=True)
+    y = sm.SubmatInvRoot.apply(vals, plan)
+    (w * y).sum().backward()
+    grad = vals.grad.detach().clone()
+    fplan = sm.submat_plan(a.rowptr, a.colind, 2, precision="fp64")
+
+    def loss(x):
+        return float((w * sm.submat_invroot(fplan, x)).sum())
+
+    h = 1e-6
+    base = torch.tensor(a.vals, device="cuda")
+    for seed in range(4):
+        e = torch.tensor(wl.random_on_pattern(a, seed=100 + seed, symmetric=True), device="cuda")
+        e /= e.norm()
+        fd = (loss(base + h * e) - loss(base - h * e)) / (2 * h)
+        ad = float((grad * e).sum())
+        assert abs(fd - ad) <= 1e-6 * max(1.0, abs(fd)), (seed, fd, ad)

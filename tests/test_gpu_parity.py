@@ -1,0 +1,235 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Error metric: per row j, ||y_j - y_j^oracle||_2 / ||y_j^oracle||_2, maximum over the rows
+checked.  Bars: 1e-10 on the FP64 path, 1e-6 on the mixed-precision path; integer plan
+bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def sm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1710_10899_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+def row_errors(a, y, ref, rows):
+    errs = []
+    for j in rows:
+        s = slice(a.rowptr[j], a.rowptr[j + 1])
+        errs.append(np.linalg.norm(y[s] - ref[s]) / np.linalg.norm(ref[s]))
+    return np.array(errs)
+
+
+def run(sm, a, p, precision, **kw):
+    plan = sm.submat_plan(a.rowptr, a.colind, p, precision=precision, **kw)
+    v = torch.tensor(a.vals, device="cuda", dtype=torch.float64)
+    y = sm.submat_invroot(plan, v, sync=True)
+    torch.cuda.synchronize()
+    return plan, y.cpu().numpy()
+
+
+def sample_rows(a, k, seed=0):
+    m = a.row_sizes()
+    rng = np.random.default_rng(seed)
+    rows = set(rng.choice(a.n, size=min(k, a.n), replace=False).tolist())
+    rows |= {int(np.argmin(m)), int(np.argmax(m))}
+    return sorted(rows)
+
+
+def test_plan_rows_bitexact(sm):
+    for a in [wl.overlap_small(), wl.random_sparse_spd(50, 0.2, seed=3),
+              wl.overlap_uniform(n=3000)]:
+        plan = sm.submat_plan(a.rowptr, a.colind, 2)
+        m, pos = plan.rows()
+        mo, po = oracle.plan(a.rowptr, a.colind)
+        np.testing.assert_array_equal(m, mo)
+        np.testing.assert_array_equal(pos, po)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_small_workload_all_rows(sm, precision):
+    a = wl.overlap_small()                       # n=2000, m 1..27, p=2
+    plan, y = run(sm, a, 2, precision)
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, 2)
+    err = row_errors(a, y, ref, range(a.n))
+    assert err.max() <= TOL[precision], err.max()
+    rep = plan.report()
+    assert rep["n_notspd"] == 0
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_uniform_sampled(sm, p, precision):
+    a = wl.overlap_uniform(n=4096)               # m 31..240: several tiles, ragged tails
+    plan, y = run(sm, a, p, precision)
+    rows = sample_rows(a, 150, seed=p)
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, p, rows=rows)
+    err = row_errors(a, y, ref, rows)
+    assert err.max() <= TOL[precision], err.max()
+    assert np.isfinite(y).all()
+
+
+def test_full_size_uniform_sampled(sm):
+    a = wl.overlap_uniform()                     # n=32768, m 32..255, kappa 1e3
+    plan, y = run(sm, a, 2, "mixed")
+    rows = sample_rows(a, 120, seed=5)
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, 2, rows=rows)
+    err = row_errors(a, y, ref, rows)
+    assert err.max() <= TOL["mixed"], err.max()
+    assert np.isfinite(y).all()
+    rep = plan.report()
+    assert rep["n_notspd"] == 0 and rep["n_rows"] == a.n
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_edge_patterns(sm, precision):
+    rng = np.random.default_rng(4)
+    cases = []
+    d = rng.uniform(0.5, 4.0, 37)
+    cases.append(wl.dense_to_csr(np.diag(d)))                                    # m = 1
+    off = rng.uniform(-0.9, 0.9, 39)
+    cases.append(wl.dense_to_csr(np.diag(rng.uniform(2, 3, 40)) + np.diag(off, 1)
+                                 + np.diag(off, -1)))                            # m = 2, 3
+    b = rng.standard_normal((70, 70))
+    dense = b @ b.T / 70 + np.eye(70)
+    cases.append(wl.dense_to_csr(dense, keep=np.ones((70, 70), dtype=bool)))     # one size
+    import scipy.linalg as sl
+    blocks = []
+    for s in [1, 5, 64, 65, 129]:
+        q = rng.standard_normal((s, s))
+        blocks.append(q @ q.T / s + 0.5 * np.eye(s))
+    cases.append(wl.dense_to_csr(sl.block_diag(*blocks),
+                                 keep=sl.block_diag(*[np.ones((s, s), bool) for s in
+                                                      [1, 5, 64, 65, 129]])))
+    for a in cases:
+        for p in (1, 2):
+            plan, y = run(sm, a, p, precision)
+            ref = oracle.invroot(a.rowptr, a.colind, a.vals, p)
+            err = row_errors(a, y, ref, range(a.n))
+            assert err.max() <= TOL[precision], (a.name, p, err.max())
+
+
+def test_dense_pattern_equals_full_root(sm):
+    import scipy.linalg as sl
+    rng = np.random.default_rng(9)
+    b = rng.standard_normal((100, 100))
+    dense = b @ b.T / 100 + 0.3 * np.eye(100)
+    a = wl.dense_to_csr(dense, keep=np.ones((100, 100), dtype=bool))
+    plan, y = run(sm, a, 2, "mixed")
+    full = np.real(sl.fractional_matrix_power(dense, -0.5))
+    yd = oracle.to_dense(a.n, a.rowptr, a.colind, y)
+    assert np.abs(yd - full.T).max() / np.abs(full).max() < 1e-6
+
+
+def test_forced_fallback_matches_oracle(sm):
+    a = wl.overlap_uniform(n=1500)
+    plan, y = run(sm, a, 2, "mixed", resid_tol=1e-300)
+    rep = plan.report()
+    assert rep["n_fallback"] == a.n
+    rows = sample_rows(a, 80)
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, 2, rows=rows)
+    assert row_errors(a, y, ref, rows).max() <= 1e-10
+
+
+def test_not_spd_rows_are_nan_and_reported(sm):
+    a = wl.overlap_small(n=500)
+    vals = a.vals.copy()
+    j = 17
+    d = a.rowptr[j] + int(np.nonzero(a.colind[a.rowptr[j]:a.rowptr[j + 1]] == j)[0][0])
+    vals[d] = -50.0
+    plan = sm.submat_plan(a.rowptr, a.colind, 2)
+    v = torch.tensor(vals, device="cuda")
+    with pytest.raises(sm.SubmatError) as ei:
+        sm.submat_invroot(plan, v, sync=True)
+    assert ei.value.name == "SUBMAT_ENOTSPD"
+    y = sm.submat_invroot(plan, v).cpu().numpy()
+    torch.cuda.synchronize()
+    bad = [r for r in range(a.n) if np.isnan(y[a.rowptr[r]:a.rowptr[r + 1]]).any()]
+    assert j in bad
+    # every submatrix containing row/column 17 is affected; all others are finite & right
+    affected = {r for r in range(a.n) if 17 in a.colind[a.rowptr[r]:a.rowptr[r + 1]]}
+    assert set(bad) <= affected
+    good = [r for r in range(a.n) if r not in affected][:60]
+    ref = oracle.invroot(a.rowptr, a.colind, vals, 2, rows=good)
+    assert row_errors(a, y, ref, good).max() <= 1e-6
+
+
+def test_nan_input_reported(sm):
+    a = wl.overlap_small(n=300)
+    vals = a.vals.copy()
+    vals[5] = np.nan
+    plan = sm.submat_plan(a.rowptr, a.colind, 2)
+    with pytest.raises(sm.SubmatError) as ei:
+        sm.submat_invroot(plan, torch.tensor(vals, device="cuda"), sync=True)
+    assert ei.value.name == "SUBMAT_ENOTSPD"
+
+
+def test_graph_and_stream_paths_agree(sm):
+    a = wl.overlap_uniform(n=2000)
+    v = torch.tensor(a.vals, device="cuda")
+    p1 = sm.submat_plan(a.rowptr, a.colind, 2, use_graph=True)
+    p2 = sm.submat_plan(a.rowptr, a.colind, 2, use_graph=False)
+    y1 = sm.submat_invroot(p1, v)
+    y1b = sm.submat_invroot(p1, v)           # graph replay
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        y2 = sm.submat_invroot(p2, v, stream=s)
+    s.synchronize()
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y1b)
+    assert torch.equal(y1, y2)
+
+
+def test_device_pattern_input(sm):
+    a = wl.overlap_small(n=700)
+    rp = torch.tensor(a.rowptr, device="cuda")
+    ci = torch.tensor(a.colind, device="cuda")
+    plan = sm.submat_plan(rp, ci, 2)
+    m, pos = plan.rows()
+    mo, po = oracle.plan(a.rowptr, a.colind)
+    np.testing.assert_array_equal(m, mo)
+    np.testing.assert_array_equal(pos, po)
+
+
+def test_invalid_calls(sm):
+    a = wl.overlap_small(n=200)
+    plan = sm.submat_plan(a.rowptr, a.colind, 2)
+    v = torch.tensor(a.vals, device="cuda")
+    st = plan._lib.submat_invroot(plan._h, v.data_ptr(), v.data_ptr(), None, 1)
+    assert sm.STATUS[st] == "SUBMAT_EINVAL"           # vals_out overlapping vals_in
+    nofwd = sm.submat_plan(a.rowptr, a.colind, 2)
+    with pytest.raises(sm.SubmatError) as ei:
+        sm.submat_invroot_backward(nofwd, v)
+    assert ei.value.name == "SUBMAT_ENOFWD"
+    # non-symmetric pattern / missing diagonal / unsorted
+    dense = np.eye(4) * 2
+    dense[0, 1] = 0.5
+    c = wl.dense_to_csr(dense)
+    with pytest.raises(sm.SubmatError) as ei:
+        sm.submat_plan(c.rowptr, c.colind, 2)
+    assert ei.value.name == "SUBMAT_ENOTSYM"
+    keep = np.ones((3, 3), bool)
+    keep[1, 1] = False
+    c = wl.dense_to_csr(np.ones((3, 3)), keep=keep)
+    with pytest.raises(sm.SubmatError) as ei:
+        sm.submat_plan(c.rowptr, c.colind, 2)
+    assert ei.value.name == "SUBMAT_ENODIAG"
+    c = wl.dense_to_csr(np.ones((3, 3)) + np.eye(3))
+    ci = c.colind.copy()
+    ci[0], ci[1] = ci[1], ci[0]
+    with pytest.raises(sm.SubmatError) as ei:
+        sm.submat_plan(c.rowptr, ci, 2)
+    assert ei.value.name == "SUBMAT_EINVAL"
