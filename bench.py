@@ -23,6 +23,11 @@ import subprocess
 import sys
 import time
 
+# The oracle baseline runs one single-threaded process per core: pin the BLAS pools to one
+# thread before numpy is first imported (the workers are forked from this process).
+for _k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ[_k] = "1"
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -42,6 +47,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=20.0)
+    ap.add_argument("--n", type=int, default=0, help="scale the workload down to n rows")
     return ap.parse_args()
 
 
@@ -59,8 +65,6 @@ _W = {}
 
 
 def _oracle_init(rowptr, colind, vals, p):
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[k] = "1"
     _W.update(rowptr=rowptr, colind=colind, vals=vals, p=p)
 
 
@@ -70,9 +74,22 @@ def _oracle_rows(rows):
     return len(rows)
 
 
+def log(msg):
+    sys.stderr.write(f"[bench {time.strftime('%H:%M:%S')}] {msg}\n")
+    sys.stderr.flush()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 def time_oracle(a, p, seconds, seed=3):
-    """The oracle as it stands, one process per host core (spawn), on a row sample sized for
-    about ``seconds`` of CPU work.  Returns (rows/s, cores, sample description)."""
+    """The oracle as it stands, one single-threaded process per host core, on a row sample
+    sized for about ``seconds`` of CPU work.  Returns (rows/s, cores, sample description).
+    The pool is forked before this process makes any CUDA call."""
     import multiprocessing as mp
     import numpy as np
     import oracle
@@ -86,14 +103,14 @@ def time_oracle(a, p, seconds, seed=3):
         oracle.row_segment(a.rowptr, a.colind, a.vals, p, int(perm[k0]))
         k0 += 1
     per_row = (time.perf_counter() - t0) / max(k0, 1)
-    cores = os.cpu_count() or 1
+    cores = min(host_cores(), 64)
     k = int(min(a.n, max(cores, seconds / per_row)))
     rows = [int(r) for r in perm[:k]]
     chunks = [rows[i::cores * 4] for i in range(cores * 4)]
     chunks = [c for c in chunks if c]
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(cores, initializer=_oracle_init,
-                  initargs=(a.rowptr, a.colind, a.vals, p)) as pool:
+    _oracle_init(a.rowptr, a.colind, a.vals, p)       # inherited by the forked workers
+    ctx = mp.get_context("fork")
+    with ctx.Pool(cores) as pool:
         pool.map(_oracle_rows, [[rows[0]]] * cores)          # warm the workers
         t0 = time.perf_counter()
         done = sum(pool.map(_oracle_rows, chunks))
@@ -104,11 +121,11 @@ def time_oracle(a, p, seconds, seed=3):
 
 
 # ----------------------------------------------------------------------------------------
-def make_workload(name, p):
+def make_workload(name, p, n=0):
     import workloads as wl
     if name not in wl.WORKLOADS:
         raise SystemExit(f"unknown workload {name}")
-    return wl.WORKLOADS[name]()
+    return wl.WORKLOADS[name](n=n) if n > 0 else wl.WORKLOADS[name]()
 
 
 def clocks_start():
@@ -167,7 +184,7 @@ def peaks():
 def traffic_for(kernel_src):
     """DRAM bytes per launch of the main kernel from the committed ncu summary, if the
     kernel source is unchanged since it was captured (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "fwd_mixed_kernel_traffic.json")
     try:
         rec = json.load(open(path))
     except Exception:
@@ -184,8 +201,10 @@ def main():
     rank, world, local = dist_env()
     import numpy as np
 
-    a = make_workload(args.workload, args.p)
+    log(f"generating {args.workload}")
+    a = make_workload(args.workload, args.p, args.n)
     p = args.p
+    log(f"n={a.n} nnz={a.nnz}")
     workload_name = f"{args.workload}(n={a.n},nnz={a.nnz},p={p})"
 
     if args.impl == "reference":
@@ -216,9 +235,13 @@ def main():
     cpu_base = None
     if rank == 0 and world == 1:
         # time the oracle before any GPU work starts the CUDA context in the pool's parent
+        log("timing the oracle on the host cores")
         cpu_base = time_oracle(a, p, args.oracle_seconds)
+        log(f"oracle: {cpu_base[0]:.1f} rows/s on {cpu_base[1]} cores")
 
+    log("plan")
     plan = sm.submat_plan(a.rowptr, a.colind, p, precision=args.precision)
+    log("warm-up")
     vals = torch.tensor(a.vals, device=dev)
     out = torch.empty_like(vals)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -259,6 +282,7 @@ def main():
     rows_total = a.n * world
     value = rows_total / (ms_per_step / 1e3)
 
+    log(f"timed: {ms_per_step:.2f} ms/step")
     # ---- accuracy on sampled rows (outside the timed region) ----------------------------
     y = out.cpu().numpy()
     max_err = None
@@ -291,13 +315,13 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_step = float(t.item())
 
+    log(f"e2e: {e2e_step:.2f} ms/step")
     # ---- the all-FP64 GPU path on the same input (one step, for the comparison) ----------
     fp64 = None
     if rank == 0 and not args.no_fp64_compare and args.precision == "mixed":
+        log("FP64 path (one step)")
         pl64 = sm.submat_plan(a.rowptr, a.colind, p, precision="fp64")
         o64 = torch.empty_like(vals)
-        sm.submat_invroot(pl64, vals, o64)
-        torch.cuda.synchronize()
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -306,6 +330,7 @@ def main():
         e1.record(stream)
         e1.synchronize()
         ms64 = e0.elapsed_time(e1)
+        log(f"FP64 path: {ms64:.1f} ms")
         r64 = pl64.report()
         d = (out - o64).cpu().numpy()
         y64 = o64.cpu().numpy()
