@@ -166,6 +166,42 @@ SUBMAT_API submat_status submat_plan_rows(submat_plan_t plan, int32_t* m, int32_
 /* Order n and entry count nnz of the plan's pattern. */
 SUBMAT_API submat_status submat_plan_shape(submat_plan_t plan, int32_t* n, int64_t* nnz);
 
+/*
+ * No-allocation forward (the paper has no counterpart; it is a deployment aid).
+ *
+ * Some callers cannot call cudaMalloc: code running inside another framework's memory pool
+ * or arena, allocation-free sections of an application, or hosts that forbid device
+ * allocations after start-up.  submat_plan allocates, so such callers use this call
+ * instead: it needs no plan and allocates nothing.  It runs the FP64 path (gather,
+ * Gershgorin scaling, coupled Newton iteration in FP64, FP64 column refinement, and the
+ * FP64 Jacobi eigendecomposition for rows whose residual test fails) with its working
+ * storage in one file-scope device array of SUBMAT_NOALLOC_SCRATCH_MIB MiB, which every GPU
+ * that loads the library holds until the process exits.
+ *
+ *   n, nnz, rowptr, colind  A's pattern in device memory (sorted, unique, symmetric, every
+ *                           diagonal stored; not re-checked here, see submat_plan)
+ *   p                       root order, >= 1
+ *   m_max                   the caller's bound on the row lengths, 1..SUBMAT_NOALLOC_MAX_M;
+ *                           larger values return SUBMAT_ETOOBIG before any GPU work, and a
+ *                           row longer than m_max (or empty) gets NaN and SUBMAT_ETOOBIG
+ *   vals_in, vals_out       device arrays of nnz doubles, not overlapping
+ *   stream                  cudaStream_t; the call is synchronous (it waits for the stream)
+ *
+ * Returns SUBMAT_ENODIAG / SUBMAT_ENOTSPD as the plan-based calls do (affected rows NaN).
+ * The first call on a device looks up the array's device address and sets the kernel's
+ * shared-memory limit on that device; make that first call before any stream capture.
+ * Every call shares the array, and the array keeps the last call's contents (the call
+ * clears its own control block): calls that overlap on the GPU race, so serialise them.
+ * It uses at most as many CTAs as the array has slots for pad(m_max) (about 18 for
+ * m_max = 256), so it is slower than submat_invroot.
+ */
+#define SUBMAT_NOALLOC_SCRATCH_MIB 64
+#define SUBMAT_NOALLOC_MAX_M 1024
+SUBMAT_API submat_status submat_invroot_noalloc(int32_t n, int64_t nnz, const int32_t* rowptr,
+                                                const int32_t* colind, int32_t p, int32_t m_max,
+                                                const double* vals_in, double* vals_out,
+                                                void* stream);
+
 /* Release every resource of the plan.  NULL is ignored. */
 SUBMAT_API void submat_plan_destroy(submat_plan_t plan);
 

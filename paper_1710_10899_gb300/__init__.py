@@ -67,7 +67,7 @@ class Report(ctypes.Structure):
 EXPORTS = ["submat_default_opts", "submat_plan", "submat_invroot", "submat_invroot_host",
            "submat_invroot_backward",
            "submat_get_report", "submat_plan_rows", "submat_plan_shape", "submat_plan_destroy",
-           "submat_status_string", "submat_last_error"]
+           "submat_status_string", "submat_last_error", "submat_invroot_noalloc"]
 
 _lib_handle = None
 
@@ -103,6 +103,8 @@ def load_library(path: str = LIB_PATH):
     lib.submat_status_string.restype = ctypes.c_char_p
     lib.submat_last_error.argtypes = []
     lib.submat_last_error.restype = ctypes.c_char_p
+    lib.submat_invroot_noalloc.argtypes = [i32, ctypes.c_int64, vp, vp, i32, i32, vp, vp, vp]
+    lib.submat_invroot_noalloc.restype = i32
     _lib_handle = lib
     return lib
 
@@ -245,6 +247,37 @@ def submat_invroot(plan: Plan, vals_in, vals_out=None, stream=None, sync: bool =
 def submat_invroot_backward(plan: Plan, grad_out, grad_in=None, stream=None):
     """``submat_invroot_backward``: gradient w.r.t. A's stored values (last forward)."""
     return plan.backward(grad_out, grad_in, stream)
+
+
+SUBMAT_NOALLOC_MAX_M = 1024
+
+
+def submat_invroot_noalloc(rowptr, colind, p: int, vals_in, vals_out=None, m_max: int = 0,
+                           stream=None):
+    """``submat_invroot_noalloc``: the FP64 forward without a plan and without any device
+    allocation by the library (its working storage is a fixed device array inside
+    libsubmat.so).  For callers that cannot allocate device memory; pass ``vals_out`` to
+    keep this call free of allocations on the Python side too.  rowptr, colind, vals_in and
+    vals_out are CUDA tensors; m_max bounds the row lengths (default: computed here, which
+    reads rowptr back to the host).  Synchronous."""
+    torch = _torch()
+    lib = load_library()
+    for t in (rowptr, colind, vals_in):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError("expected CUDA tensors")
+    if rowptr.dtype != torch.int32 or colind.dtype != torch.int32 or vals_in.dtype != torch.float64:
+        raise TypeError("expected int32 rowptr/colind and float64 values")
+    n = rowptr.numel() - 1
+    if m_max <= 0:
+        m_max = int((rowptr[1:] - rowptr[:-1]).max().item()) if n > 0 else 1
+    if vals_out is None:
+        vals_out = torch.empty_like(vals_in)
+    _check(lib, lib.submat_invroot_noalloc(n, colind.numel(), ctypes.c_void_p(rowptr.data_ptr()),
+                                           ctypes.c_void_p(colind.data_ptr()), int(p), int(m_max),
+                                           ctypes.c_void_p(vals_in.data_ptr()),
+                                           ctypes.c_void_p(vals_out.data_ptr()),
+                                           _stream_ptr(stream)))
+    return vals_out
 
 
 def _make_function():

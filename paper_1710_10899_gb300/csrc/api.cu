@@ -43,6 +43,10 @@ struct GraphEntry {
 
 }  // namespace
 
+namespace submat {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace submat
+
 struct submat_plan_s {
   int device = 0;
   int n_sm = 0;

@@ -81,7 +81,8 @@ size_t smem_fwd_mixed();
 size_t smem_fwd_fp64();
 size_t smem_fallback();
 size_t smem_backward();
-cudaError_t set_kernel_attributes();
+// Message returned by submat_last_error() on this thread.
+void set_last_error(const std::string& msg);
 
 // Per-CTA scratch bytes for a padded order mp (and true order m <= mp).
 size_t scratch_mixed(int mp);

@@ -4,81 +4,12 @@
 // mixed-precision path is measured against.
 #include "common.cuh"
 #include "refine.cuh"
+#include "fp64_gemm.cuh"
 
 namespace submat {
 namespace {
 
-constexpr int TB = 64;     // output tile
-constexpr int TK = 16;     // k-slice
-
-enum Epi { EPI_STORE = 0, EPI_M = 1 };
-
-// C = A B for FP64 mp x mp matrices (row-major, ld mp).  EPI_M also writes
-// Tn = ((p+1) I - C)/p on the leading m x m block (zero elsewhere) and adds
-// sum (C - I)^2 over that block to *norm2_s.
-__device__ void gemm64(const double* __restrict__ A, const double* __restrict__ B,
-                       double* __restrict__ C, int mp, int m, int epi, double* __restrict__ Tn,
-                       int p, double* smem, double* norm2_s) {
-  double* As = smem;                 // [TK][TB]
-  double* Bs = smem + TK * TB;       // [TK][TB]
-  const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
-  const int nt = mp / TB;
-  double nrm = 0.0;
-  for (int t = 0; t < nt * nt; ++t) {
-    const int i0 = (t / nt) * TB, j0 = (t % nt) * TB;
-    double acc[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
-    for (int k0 = 0; k0 < mp; k0 += TK) {
-#pragma unroll
-      for (int q = 0; q < (TB * TK) / kThreads; ++q) {
-        const int e = tid + q * kThreads;
-        const int ii = e / TK, kk = e % TK;
-        As[kk * TB + ii] = A[(size_t)(i0 + ii) * mp + k0 + kk];
-        const int kb = e / TB, jj = e % TB;
-        Bs[kb * TB + jj] = B[(size_t)(k0 + kb) * mp + j0 + jj];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < TK; ++kk) {
-        double av[4], bv[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) av[r] = As[kk * TB + ty + 16 * r];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) bv[c] = Bs[kk * TB + tx + 16 * c];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int i = i0 + ty + 16 * r, jj = j0 + tx + 16 * c;
-        const size_t idx = (size_t)i * mp + jj;
-        const double v = acc[r][c];
-        C[idx] = v;
-        if (epi == EPI_M) {
-          const bool in = (i < m) && (jj < m);
-          const double d = (i == jj) ? 1.0 : 0.0;
-          Tn[idx] = in ? ((double)(p + 1) * d - v) / (double)p : 0.0;
-          const double e = in ? v - d : 0.0;
-          nrm += e * e;
-        }
-      }
-  }
-  if (epi == EPI_M) {
-    nrm = warp_sum(nrm);
-    if ((tid & 31) == 0) atomicAdd(norm2_s, nrm);
-  }
-  __syncthreads();
-}
+using namespace fp64;
 
 __global__ void __launch_bounds__(kThreads, 1) fwd_fp64_kernel(FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -64,3 +64,12 @@ def test_host_side_validation(lib):
     big = 1537
     assert _plan_status(lib, [0, big], np.arange(big)) == "SUBMAT_ETOOBIG"
     assert lib.submat_plan(None, 2, None, None) != 0
+
+
+def test_noalloc_host_side_validation(lib):
+    import paper_1710_10899_gb300 as pkg
+    st = lib.submat_invroot_noalloc(4, 4, 1, 1, 2, pkg.SUBMAT_NOALLOC_MAX_M + 1, 1, 1 << 20, None)
+    assert pkg.STATUS[st] == "SUBMAT_ETOOBIG"
+    assert pkg.STATUS[lib.submat_invroot_noalloc(4, 4, 1, 1, 0, 8, 1, 1 << 20, None)] == "SUBMAT_EINVAL"
+    assert pkg.STATUS[lib.submat_invroot_noalloc(4, 4, 1, 1, 2, 8, 1, 1, None)] == "SUBMAT_EINVAL"
+    assert pkg.STATUS[lib.submat_invroot_noalloc(0, 0, None, None, 2, 8, None, None, None)] == "SUBMAT_OK"
