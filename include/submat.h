@@ -44,7 +44,8 @@ typedef enum {
   SUBMAT_ECUDA = 6,     /* a CUDA runtime call failed (the message is in submat_last_error) */
   SUBMAT_ENOTSPD = 7,   /* some submatrix is not positive definite or holds a non-finite
                            value; its output row is NaN, the others are valid            */
-  SUBMAT_ENOFWD = 8     /* backward called before any forward on this plan                 */
+  SUBMAT_ENOFWD = 8,    /* backward called before any forward on this plan                 */
+  SUBMAT_ETIMEOUT = 9   /* a device-side pipeline wait gave up (the rows not done are NaN)  */
 } submat_status;
 
 /* Largest submatrix order (row length) the library accepts. */
@@ -53,9 +54,12 @@ typedef enum {
 /* Precision of the submatrix operation. */
 enum {
   SUBMAT_PREC_FP64 = 0,       /* coupled Newton iteration entirely in FP64 (CUDA cores)     */
-  SUBMAT_PREC_MIXED_F16 = 1   /* coupled Newton iteration on the tensor cores with operands
-                                 split into FP16 hi/lo pairs (three products per GEMM, FP32
-                                 accumulation), then an FP64 column refinement and check  */
+  SUBMAT_PREC_MIXED_F16 = 1,  /* coupled Newton iteration on the tensor cores (tcgen05) with
+                                 every matrix split into five FP16 planes of small integers,
+                                 accumulated exactly per level (15 FP16 MMAs per product),
+                                 then the FP64 column residual check                       */
+  SUBMAT_PREC_MIXED_F16_SYNC = 2  /* the same arithmetic on the legacy mma.sync tensor path
+                                 (kept as the baseline of the tcgen05 engine)               */
 };
 
 typedef struct {

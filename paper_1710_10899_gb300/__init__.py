@@ -23,11 +23,13 @@ LIB_PATH = os.path.join(_PKG, "libsubmat.so")
 SUBMAT_MAX_M = 1536
 PREC_FP64 = 0
 PREC_MIXED_F16 = 1
+PREC_MIXED_F16_SYNC = 2
+PRECISIONS = {"fp64": PREC_FP64, "mixed": PREC_MIXED_F16, "mixed_sync": PREC_MIXED_F16_SYNC}
 
 STATUS = {
     0: "SUBMAT_OK", 1: "SUBMAT_EINVAL", 2: "SUBMAT_ENODIAG", 3: "SUBMAT_ENOTSYM",
     4: "SUBMAT_ETOOBIG", 5: "SUBMAT_ENOMEM", 6: "SUBMAT_ECUDA", 7: "SUBMAT_ENOTSPD",
-    8: "SUBMAT_ENOFWD",
+    8: "SUBMAT_ENOFWD", 9: "SUBMAT_ETIMEOUT",
 }
 
 
@@ -153,7 +155,7 @@ class Plan:
         csr = CSR(n, nnz, rp_ptr, ci_ptr if nnz > 0 else None, on_dev)
         o = Opts()
         lib.submat_default_opts(ctypes.byref(o))
-        o.precision = {"mixed": PREC_MIXED_F16, "fp64": PREC_FP64}[precision]
+        o.precision = PRECISIONS[precision]
         o.k_max = k_max
         o.tol = tol
         o.resid_tol = resid_tol

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 
 namespace submat {
@@ -69,7 +71,9 @@ struct submat_plan_s {
   double* d_saved = nullptr;
   bool have_fwd = false;
   int32_t m_max = 0;
+  int32_t ld = 0;                     // mixed path: leading dimension of the scratch planes
   double sum_m3 = 0.0;
+  CUtensorMap tm_a{}, tm_b{};         // mixed path, tcgen05 engine
   cudaStream_t last_stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -130,6 +134,10 @@ submat_status enqueue_forward(submat_plan_t P, const double* in, double* out, cu
   a.resid_tol = P->opts.resid_tol;
   a.refine_steps = P->opts.refine_steps;
   a.kappa_max = P->opts.kappa_max;
+  a.ld = P->ld;
+  a.engine = P->opts.precision == SUBMAT_PREC_MIXED_F16_SYNC ? 1 : 0;
+  a.tm_a = P->tm_a;
+  a.tm_b = P->tm_b;
   CUDA_TRY(cudaMemcpyAsync(P->d_saved, in, (size_t)P->nnz * sizeof(double),
                            cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemsetAsync(P->d_ctr, 0, sizeof(DevCounters), s));
@@ -170,6 +178,7 @@ const char* submat_status_string(submat_status s) {
     case SUBMAT_ECUDA: return "CUDA error";
     case SUBMAT_ENOTSPD: return "submatrix not positive definite";
     case SUBMAT_ENOFWD: return "no forward on this plan";
+    case SUBMAT_ETIMEOUT: return "device pipeline wait timed out";
   }
   return "unknown status";
 }
@@ -191,7 +200,8 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   submat_opts o;
   submat_default_opts(&o);
   if (opts) o = *opts;
-  if (o.precision != SUBMAT_PREC_FP64 && o.precision != SUBMAT_PREC_MIXED_F16)
+  if (o.precision != SUBMAT_PREC_FP64 && o.precision != SUBMAT_PREC_MIXED_F16 &&
+      o.precision != SUBMAT_PREC_MIXED_F16_SYNC)
     return fail(SUBMAT_EINVAL, "unknown precision");
   if (o.k_max < 1) o.k_max = 40;
   if (!(o.tol > 0.0)) o.tol = (o.precision == SUBMAT_PREC_FP64) ? 1e-7 : 1e-4;
@@ -297,12 +307,43 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
     PLAN_TRY(cudaMemcpy(P->d_order, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
 
   const int mp = std::max(pad_mixed(m_max), pad_fp64(m_max));
-  size_t stride = std::max(scratch_eig(mp), o.precision == SUBMAT_PREC_FP64 ? scratch_fp64(mp)
-                                                                             : scratch_mixed(mp));
+  const bool mixed = o.precision != SUBMAT_PREC_FP64;
+  // mixed path: planes of LD x LD halves (LD >= one 128-row tile); 34 planes per CTA hold
+  // the six sliced matrices, S_j and, for the fallback, 3 m^2 doubles
+  P->ld = std::max(128, mp);
+  size_t stride = mixed ? scratch_mixed(P->ld) : std::max(scratch_eig(mp), scratch_fp64(mp));
   stride = (stride + 1023) / 1024 * 1024;
   P->stride = stride;
   P->grid = std::max(1, std::min(P->n_sm, n));
   PLAN_TRY(cudaMalloc(&P->d_scratch, stride * (size_t)P->grid));
+  if (mixed && o.precision == SUBMAT_PREC_MIXED_F16) {
+    // TMA descriptors over all CTAs' planes: dims (LD cols, LD rows, planes), 64-byte swizzle
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t ge = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled",
+                                             reinterpret_cast<void**>(&encode),
+                                             cudaEnableDefault, &q);
+    if (ge != cudaSuccess || q != cudaDriverEntryPointSuccess || !encode) {
+      fail(SUBMAT_ECUDA, "cuTensorMapEncodeTiled not available");
+      return bail(SUBMAT_ECUDA);
+    }
+    const uint64_t planes = (uint64_t)(stride / ((size_t)P->ld * P->ld * 2)) * P->grid;
+    cuuint64_t dims[3] = {(cuuint64_t)P->ld, (cuuint64_t)P->ld, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)P->ld * 2, (cuuint64_t)P->ld * P->ld * 2};
+    cuuint32_t elem[3] = {1, 1, 1};
+    cuuint32_t box_a[3] = {32, 128, 1}, box_b[3] = {32, 64, 1};
+    CUresult r1 = encode(&P->tm_a, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, P->d_scratch, dims, strides,
+                         box_a, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r2 = encode(&P->tm_b, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, P->d_scratch, dims, strides,
+                         box_b, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+      fail(SUBMAT_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r1) + ", " +
+                             std::to_string((int)r2) + ")");
+      return bail(SUBMAT_ECUDA);
+    }
+  }
   PLAN_TRY(cudaMalloc(&P->d_saved, (nnz > 0 ? nnz : 1) * sizeof(double)));
   PLAN_TRY(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   for (auto& e : P->ev) PLAN_TRY(cudaEventCreate(&e));
@@ -365,6 +406,7 @@ submat_status submat_invroot(submat_plan_t P, const double* in, double* out, voi
     CUDA_TRY(cudaStreamSynchronize(s));
     DevCounters c;
     CUDA_TRY(cudaMemcpy(&c, P->d_ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    if (c.error) return fail(SUBMAT_ETIMEOUT, "a device pipeline wait timed out");
     if (c.n_notspd > 0)
       return fail(SUBMAT_ENOTSPD, std::to_string(c.n_notspd) + " submatrices not SPD");
   }

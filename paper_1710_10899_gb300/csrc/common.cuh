@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libsubmat.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -26,10 +27,15 @@ struct DevCounters {
   double flops_fp64;
   double flops_tensor;
   unsigned long long n_illcond;        // rows sent to the fallback by the condition estimate
+  int32_t error;                       // a device pipeline wait timed out
 };
 
 // Arguments of the forward kernels.
 struct FwdArgs {
+  CUtensorMap tm_a;          // mixed tcgen05 engine: A tiles (32 x 128) of the scratch planes
+  CUtensorMap tm_b;          //                       B tiles (32 x 64)
+  int32_t ld;                // mixed path: leading dimension of the scratch planes
+  int32_t engine;            // mixed path: 0 = tcgen05, 1 = mma.sync
   const int32_t* rowptr;
   const int32_t* colind;
   const int32_t* m;          // [n] row sizes
@@ -84,8 +90,8 @@ size_t smem_backward();
 // Message returned by submat_last_error() on this thread.
 void set_last_error(const std::string& msg);
 
-// Per-CTA scratch bytes for a padded order mp (and true order m <= mp).
-size_t scratch_mixed(int mp);
+// Per-CTA scratch bytes: mixed path for plane leading dimension ld, others for order mp.
+size_t scratch_mixed(int ld);
 size_t scratch_fp64(int mp);
 size_t scratch_eig(int mp);
 

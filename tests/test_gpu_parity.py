@@ -233,3 +233,17 @@ def test_invalid_calls(sm):
     with pytest.raises(sm.SubmatError) as ei:
         sm.submat_plan(c.rowptr, ci, 2)
     assert ei.value.name == "SUBMAT_EINVAL"
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_tcgen05_and_mma_sync_engines_agree(sm, p):
+    # same arithmetic on two tensor-core engines; both must meet the bar against the oracle
+    a = wl.overlap_uniform(n=3000)
+    rows = sample_rows(a, 60, seed=10 + p)
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, p, rows=rows)
+    outs = {}
+    for prec in ("mixed", "mixed_sync"):
+        plan, y = run(sm, a, p, prec)
+        assert row_errors(a, y, ref, rows).max() <= TOL["mixed"]
+        outs[prec] = y
+    assert row_errors(a, outs["mixed"], outs["mixed_sync"], range(a.n)).max() <= 1e-6
