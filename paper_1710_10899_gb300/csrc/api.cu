@@ -331,7 +331,7 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
     cuuint64_t dims[3] = {(cuuint64_t)P->ld, (cuuint64_t)P->ld, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)P->ld * 2, (cuuint64_t)P->ld * P->ld * 2};
     cuuint32_t elem[3] = {1, 1, 1};
-    cuuint32_t box_a[3] = {32, 128, 1}, box_b[3] = {32, 64, 1};
+    cuuint32_t box_a[3] = {32, 128, 1}, box_b[3] = {32, 48, 1};
     CUresult r1 = encode(&P->tm_a, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, P->d_scratch, dims, strides,
                          box_a, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

@@ -14,6 +14,8 @@ namespace submat {
 
 constexpr int kThreads = 256;          // threads per CTA of the per-submatrix kernels
 constexpr int kWarps = kThreads / 32;
+constexpr int kMaxWarps = 16;          // largest CTA any helper below runs in (512 threads)
+constexpr int kRedDoubles = 2 * kMaxWarps;   // shared reduction scratch of the helpers
 
 // Device-side counters of one forward / backward call (zeroed before each call).
 struct DevCounters {
@@ -33,7 +35,7 @@ struct DevCounters {
 // Arguments of the forward kernels.
 struct FwdArgs {
   CUtensorMap tm_a;          // mixed tcgen05 engine: A tiles (32 x 128) of the scratch planes
-  CUtensorMap tm_b;          //                       B tiles (32 x 64)
+  CUtensorMap tm_b;          //                       B tiles (32 x 48)
   int32_t ld;                // mixed path: leading dimension of the scratch planes
   int32_t engine;            // mixed path: 0 = tcgen05, 1 = mma.sync
   const int32_t* rowptr;
@@ -107,6 +109,8 @@ __host__ __device__ inline int pad_fp64(int m) { return (m + 63) / 64 * 64; }
 #ifdef __CUDACC__
 namespace submat {
 
+__device__ __forceinline__ int nwarps() { return (int)(blockDim.x >> 5); }
+
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -134,7 +138,7 @@ __device__ __forceinline__ int find_sorted(const int32_t* a, int len, int32_t ke
 
 // Algorithm 1 for row j (value part): S[k*m + l] = A[R[k]][R[l]] in FP64 (zero where not
 // stored), R staged in shared memory (R_s, m ints), and the Gershgorin bound
-// max_k sum_l |S_kl| returned to every thread.  red_s: kWarps doubles of shared memory.
+// max_k sum_l |S_kl| returned to every thread.  red_s: kRedDoubles doubles of shared memory.
 static __device__ double gather_submatrix(const int32_t* __restrict__ rowptr,
                                    const int32_t* __restrict__ colind,
                                    const double* __restrict__ vals, int j, int m,
@@ -145,7 +149,8 @@ static __device__ double gather_submatrix(const int32_t* __restrict__ rowptr,
   for (int e = tid; e < m * m; e += blockDim.x) S[e] = 0.0;
   __syncthreads();
   double wmax = 0.0;
-  for (int k = warp; k < m; k += kWarps) {
+  const int nw = nwarps();
+  for (int k = warp; k < m; k += nw) {
     const int r = R_s[k];
     const int b = rowptr[r], e_end = rowptr[r + 1];
     double sum = 0.0;
@@ -165,7 +170,7 @@ static __device__ double gather_submatrix(const int32_t* __restrict__ rowptr,
   if (lane == 0) red_s[warp] = wmax;
   __syncthreads();
   double lam = red_s[0];
-  for (int w = 1; w < kWarps; ++w) {
+  for (int w = 1; w < nw; ++w) {
     const double v = red_s[w];
     lam = (v != v || lam != lam) ? (v + lam) : fmax(lam, v);
   }

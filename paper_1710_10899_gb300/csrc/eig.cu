@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(kThreads) fallback_kernel(FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* cs_s = reinterpret_cast<double*>(smem_raw);               // SUBMAT_MAX_M
   double* lam_s = cs_s + SUBMAT_MAX_M;                                // SUBMAT_MAX_M
-  double* red_s = lam_s + SUBMAT_MAX_M;                               // 2*kWarps
-  int32_t* pair_s = reinterpret_cast<int32_t*>(red_s + 2 * kWarps);  // SUBMAT_MAX_M
+  double* red_s = lam_s + SUBMAT_MAX_M;                               // kRedDoubles
+  int32_t* pair_s = reinterpret_cast<int32_t*>(red_s + kRedDoubles);  // SUBMAT_MAX_M
   int32_t* R_s = pair_s + SUBMAT_MAX_M;                               // SUBMAT_MAX_M
   __shared__ int job_s;
   __shared__ int bad_s;
@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
   double* al_s = cs_s + SUBMAT_MAX_M;                                 // alpha = lambda^(1/p)
   double* u_s = al_s + SUBMAT_MAX_M;                                  // V^T g
   double* w_s = u_s + SUBMAT_MAX_M;                                   // V^T e_pos
-  double* red_s = w_s + SUBMAT_MAX_M;                                 // 2*kWarps
-  int32_t* pair_s = reinterpret_cast<int32_t*>(red_s + 2 * kWarps);  // SUBMAT_MAX_M
+  double* red_s = w_s + SUBMAT_MAX_M;                                 // kRedDoubles
+  int32_t* pair_s = reinterpret_cast<int32_t*>(red_s + kRedDoubles);  // SUBMAT_MAX_M
   int32_t* R_s = pair_s + SUBMAT_MAX_M;                               // SUBMAT_MAX_M
   __shared__ int job_s;
   __shared__ int bad_s;
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
       w_s[i] = V[pos * m + i];
     }
     // u = V^T g: one warp per component
-    for (int i = warp; i < m; i += kWarps) {
+    for (int i = warp; i < m; i += nwarps()) {
       double s = 0.0;
       for (int k = lane; k < m; k += 32) s = fma(V[k * m + i], g[k], s);
       s = warp_sum(s);
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
     }
     __syncthreads();
     // scatter-add G[k][l] into the stored entry (R[k], R[l])
-    for (int k = warp; k < m; k += kWarps) {
+    for (int k = warp; k < m; k += nwarps()) {
       const int r = R_s[k];
       for (int e = a.rowptr[r] + lane; e < a.rowptr[r + 1]; e += 32) {
         const int l = find_sorted(R_s, m, a.colind[e]);
@@ -164,10 +164,10 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
 }  // namespace
 
 size_t smem_fallback() {
-  return (2 * SUBMAT_MAX_M + 2 * kWarps) * sizeof(double) + 2 * SUBMAT_MAX_M * sizeof(int32_t);
+  return (2 * SUBMAT_MAX_M + kRedDoubles) * sizeof(double) + 2 * SUBMAT_MAX_M * sizeof(int32_t);
 }
 size_t smem_backward() {
-  return (4 * SUBMAT_MAX_M + 2 * kWarps) * sizeof(double) + 2 * SUBMAT_MAX_M * sizeof(int32_t);
+  return (4 * SUBMAT_MAX_M + kRedDoubles) * sizeof(double) + 2 * SUBMAT_MAX_M * sizeof(int32_t);
 }
 size_t scratch_eig(int mp) { return 3 * (size_t)mp * mp * sizeof(double); }
 

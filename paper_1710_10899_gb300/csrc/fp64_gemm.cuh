@@ -10,12 +10,16 @@ constexpr int TK = 16;     // k-slice
 
 enum Epi { EPI_STORE = 0, EPI_M = 1 };
 
-// C = A B for FP64 mp x mp matrices (row-major, ld mp).  EPI_M also writes
-// Tn = ((p+1) I - C)/p on the leading m x m block (zero elsewhere) and adds
-// sum (C - I)^2 over that block to *norm2_s.
+// C = A B for FP64 mp x mp matrices (row-major, ld mp), or C = yc (ya Y - A B) if Y is
+// given (the step matrix yc (ya I - A) applied to the symmetric Y).  EPI_M adds
+// sum (C - I)^2 over the leading m x m block to *norm2_s and, if Tn is given, writes the
+// next step matrix Tn = tc (ta I - C) / td there (zero elsewhere; Newton's step is
+// ta = p+1, tc = 1, td = p).
 static __device__ void gemm64(const double* __restrict__ A, const double* __restrict__ B,
                        double* __restrict__ C, int mp, int m, int epi, double* __restrict__ Tn,
-                       int p, double* smem, double* norm2_s) {
+                       double tc, double ta, double td, double* smem, double* norm2_s,
+                       const double* __restrict__ Y = nullptr, double yc = 0.0,
+                       double ya = 0.0) {
   double* As = smem;                 // [TK][TB]
   double* Bs = smem + TK * TB;       // [TK][TB]
   const int tid = threadIdx.x;
@@ -59,12 +63,12 @@ static __device__ void gemm64(const double* __restrict__ A, const double* __rest
       for (int c = 0; c < 4; ++c) {
         const int i = i0 + ty + 16 * r, jj = j0 + tx + 16 * c;
         const size_t idx = (size_t)i * mp + jj;
-        const double v = acc[r][c];
+        const double v = Y ? yc * (ya * Y[idx] - acc[r][c]) : acc[r][c];
         C[idx] = v;
         if (epi == EPI_M) {
           const bool in = (i < m) && (jj < m);
           const double d = (i == jj) ? 1.0 : 0.0;
-          Tn[idx] = in ? ((double)(p + 1) * d - v) / (double)p : 0.0;
+          if (Tn) Tn[idx] = in ? tc * (ta * d - v) / td : 0.0;
           const double e = in ? v - d : 0.0;
           nrm += e * e;
         }

@@ -2,10 +2,12 @@
 //
 // Per row j (Alg. 1, Sec. 3.2, Alg. 2):
 //   gather S_j (FP64) -> Gershgorin bound lambda_bar = max_k sum_l |S_kl| (FP64)
-//   M_0 = S/lambda_bar, X_0 = I; coupled Newton iteration for the inverse p-th root
-//       T_k = ((p+1) I - M_k) / p,  X_{k+1} = X_k T_k,  M_{k+1} = T_k^p M_k
+//   M_0 = S/lambda_bar, X_0 = I; coupled iteration for the inverse p-th root
+//       X_{k+1} = X_k T_k,  M_{k+1} = T_k^p M_k
 //   (the coupled form of the Newton iteration of Bini, Higham and Meini cited in Sec. 2)
-//   until ||M - I||_F <= tol sqrt(m), then one more X update; F = lambda_bar^(-1/p) X;
+//   with spectrally scaled steps T_k = c_k (alpha_k I - M_k) (scaled_step.cuh), until
+//   ||M - I||_F <= tol sqrt(m), then one Newton update X T, T = ((p+1) I - M)/p;
+//   F = lambda_bar^(-1/p) X;
 //   FP64 column residual (refine.cuh) and condition estimate; write column pos_j.
 //
 // Arithmetic.  Rounding errors made in any iteration persist in the coupled iteration's
@@ -15,8 +17,8 @@
 // scale per matrix (an error-free splitting in the manner of Ozaki et al.; slices.cuh):
 //     A = 2^(E-7) sum_{s<5} q_s 2^(-8s),  |q0| <= 128, |q1..q4| <= 129,
 // about 39 significant bits relative to the largest entry (E is chosen tight: M's
-// eigenvalues lie in (0,1], those of T and of T^i M in [1,2) and (0,2); X's exponent is
-// measured after every product).  A product is the sum over levels L = s + t <= 4 of
+// eigenvalues lie in (0,1], those of T and of T^i M below bounds that follow from the step
+// constants; X's exponent is predicted from its last measured maximum).  A product is the sum over levels L = s + t <= 4 of
 // 2^(-8L) sum_{s+t=L} Q_s^A Q_t^B (15 FP16 MMAs per k-step, FP32 accumulation per level).
 // The products of these integers are exact, and every level-0 partial sum is an integer
 // below 2^14 K, so for K <= 1024 the tensor cores accumulate level 0 exactly (level 1
@@ -27,10 +29,12 @@
 // per-product error, kept by every iteration, left ~6e-7 in the result; measured.)
 //
 // GEMM engines (template parameter TC):
-//   TC = true  (default): tcgen05.mma kind::f16, M = 128, N = 64, the five level
-//              accumulators in TMEM (5 x 64 of 512 columns), operands moved by TMA
+//   TC = true  (default): tcgen05.mma kind::f16, M = 128, N = 48, the five level
+//              accumulators in TMEM, double-buffered (2 x 5 x 48 of 512 columns) so the
+//              epilogue of one tile overlaps the MMAs of the next; operands moved by TMA
 //              (SWIZZLE_64B, 32-wide k-slices) through a 3-stage mbarrier pipeline.
-//              Roles: warp 0 issues TMA, warp 1 issues MMAs, warps 4-7 run the epilogue.
+//              Roles: warps 0-7 run the epilogue (two per TMEM lane quarter), warp 8
+//              issues TMA, warp 9 issues MMAs (320 threads).
 //              All working matrices are symmetric, so a row-major B read as K-major
 //              gives B^T = B to rounding: the engine computes A B^T.
 //   TC = false: mma.sync m16n8k16 on 64 x 64 tiles with a cp.async pipeline (the legacy
@@ -44,6 +48,7 @@
 #include "common.cuh"
 #include "refine.cuh"
 #include "slices.cuh"
+#include "scaled_step.cuh"
 #include "tc_prims.cuh"
 
 namespace submat {
@@ -52,11 +57,14 @@ namespace {
 using namespace slc;
 
 constexpr int E_M = 0;             // |M| <= 1 (eigenvalues of M_k lie in (0, 1])
-constexpr int E_T = 1;             // |T| <= 2 (eigenvalues of T_k lie in [1, (p+1)/p))
-constexpr int E_P = 1;             // |T^i M| <= 2 for i < p (eigenvalues below ((p+1)/p)^i < e)
-constexpr int kPlanesPerCta = 34;  // 6 matrices x 5 planes + 4 planes of room for S_j (FP64)
+constexpr int kPlanesPerCta = 35;  // 6 matrices x 5 planes, 4 planes of room for S_j (FP64),
+                                   // 1 plane for the tracked vectors
 
-enum Epi { EPI_FIXED = 0, EPI_M = 1, EPI_X = 2 };
+// Every product of the iteration has the form C = c (alpha Y - A Y'), i.e. the step matrix
+// T = c (alpha I - A) applied to Y (Y' = Y, or Y = A for the X update of p = 1): the
+// epilogue reads Y's entry at the output position (all matrices are symmetric).  Flags:
+// accumulate ||C - I||_F^2 over the leading m x m block, and/or max |C|.
+enum EpiFlag { EPI_NORM = 1, EPI_AMAX = 2 };
 
 struct Mat {
   __half* q;        // NSL planes of LD*LD halves
@@ -69,27 +77,11 @@ struct GemmIO {     // what every GEMM call shares within one submatrix
   size_t plane;     // ld * ld
   float* norm2_s;
   unsigned* amax_s;
+  float c, alpha;          // C = c (alpha Y - A B)
 };
 
-// Slices of 16 consecutive values -> two 16-byte stores per plane.
-__device__ __forceinline__ void store16_slices(__half* q, size_t plane, size_t idx0,
-                                               const float* vh, const float* vl, int e) {
-  __align__(16) __half out[NSL][16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    float s[NSL];
-    make_slices(vh[c], vl[c], e, s);
-#pragma unroll
-    for (int k = 0; k < NSL; ++k) out[k][c] = __float2half_rn(s[k]);
-  }
-#pragma unroll
-  for (int k = 0; k < NSL; ++k) {
-    uint4* dst = reinterpret_cast<uint4*>(q + k * plane + idx0);
-    const uint4* src = reinterpret_cast<const uint4*>(out[k]);
-    dst[0] = src[0];
-    dst[1] = src[1];
-  }
-}
+// Exponent for values bounded by b (with a relative margin for rounding).
+__device__ __forceinline__ int exp_of(float b) { return exp_bound(b * (1.f + 1e-6f)); }
 
 // Slices of 8 consecutive values -> one 16-byte store per plane.
 __device__ __forceinline__ void store8_slices(__half* q, size_t plane, size_t idx0,
@@ -114,7 +106,7 @@ template <int NP>
 __device__ void matvec_slices_f32(const __half* q, size_t plane, int ld, float scale,
                                   const float* x, float* y, int m, int mp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = warp; i < m; i += kWarps) {
+  for (int i = warp; i < m; i += nwarps()) {
     float acc = 0.f;
     for (int c0 = lane * 8; c0 < mp; c0 += 256) {
       const size_t e = (size_t)i * ld + c0;
@@ -138,6 +130,49 @@ __device__ void matvec_slices_f32(const __half* q, size_t plane, int ld, float s
   __syncthreads();
 }
 
+// out[i] = sum_k A(i,k) x[k] for i < m, A from all NSL planes (scale exponent e), x given as
+// double-floats (xh, xl) zero beyond m up to mp; the result in FP64.  The planes' integers
+// recombine exactly (a = q0 2^8 + q1, b = q2 2^16 + q3 2^8 + q4, A = 2^(e-15) (a + 2^-24 b))
+// and the products a xh are accumulated error-free in double-float, so the sum keeps about
+// 44 bits.  One warp per row, eight consecutive columns per lane.
+__device__ void matvec_slices_df(const __half* q, size_t plane, int ld, int e, const float* xh,
+                                 const float* xl, double* out, int m, int mp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double sc = ldexp(1.0, e - 15);
+  for (int i = warp; i < m; i += nwarps()) {
+    float sh = 0.f, sl = 0.f;
+    for (int c0 = lane * 8; c0 < mp; c0 += 256) {
+      const size_t g = (size_t)i * ld + c0;
+      uint4 raw[NSL];
+#pragma unroll
+      for (int k = 0; k < NSL; ++k) raw[k] = *reinterpret_cast<const uint4*>(q + k * plane + g);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        float qq[NSL];
+#pragma unroll
+        for (int k = 0; k < NSL; ++k) qq[k] = __half2float(reinterpret_cast<const __half*>(&raw[k])[c]);
+        const float a = __fmaf_rn(qq[0], 256.f, qq[1]);
+        const float b = __fmaf_rn(qq[2], 65536.f, __fmaf_rn(qq[3], 256.f, qq[4]));
+        const float x = xh[c0 + c];
+        const float pr = __fmul_rn(a, x);
+        const float pe = __fmaf_rn(a, x, -pr);          // a x - pr exactly
+        float t;
+        two_sum(sh, pr, sh, t);
+        sl = __fadd_rn(sl, __fadd_rn(t, __fmaf_rn(a, xl[c0 + c], __fmaf_rn(b * (1.f / 16777216.f), x, pe))));
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
+      float t;
+      two_sum(sh, oh, sh, t);
+      sl = __fadd_rn(sl, __fadd_rn(ol, t));
+    }
+    if (lane == 0) out[i] = ((double)sh + (double)sl) * sc;
+  }
+  __syncthreads();
+}
+
 // Largest eigenvalue of the SPD X (power method, FP32, two leading planes).
 __device__ float power_max_slices(const __half* q, size_t plane, int ld, float scale, int m,
                                   int mp, float* a_s, float* b_s, float* red_s, int iters) {
@@ -153,10 +188,10 @@ __device__ float power_max_slices(const __half* q, size_t plane, int ld, float s
     for (int i = tid; i < m; i += blockDim.x) { na += a_s[i] * a_s[i]; nb += b_s[i] * b_s[i]; }
     na = warp_sum_f(na);
     nb = warp_sum_f(nb);
-    if (lane == 0) { red_s[warp] = na; red_s[kWarps + warp] = nb; }
+    if (lane == 0) { red_s[warp] = na; red_s[kMaxWarps + warp] = nb; }
     __syncthreads();
     float ta = 0.f, tb = 0.f;
-    for (int w = 0; w < kWarps; ++w) { ta += red_s[w]; tb += red_s[kWarps + w]; }
+    for (int w = 0; w < nwarps(); ++w) { ta += red_s[w]; tb += red_s[kMaxWarps + w]; }
     lam = sqrtf(tb / ta);
     const float inv = tb > 0.f ? rsqrtf(tb) : 0.f;
     for (int i = tid; i < m; i += blockDim.x) a_s[i] = b_s[i] * inv;
@@ -165,50 +200,63 @@ __device__ float power_max_slices(const __half* q, size_t plane, int ld, float s
   return lam;
 }
 
-// Residual ||e_pos - F^p s_pos||_2 of the converged iterate F = c X (p >= 2, no column step):
-// a failure test against a threshold of order 1e-3, so FP32 with three planes suffices.
-__device__ float column_residual_f32(const __half* q, size_t plane, int ld, float xscale,
-                                     double c, const double* S, int m, int mp, int pos, int p,
-                                     float* a_s, float* b_s, float* red_s) {
+// Starting lower end of M_0's spectrum (scaled_step.cuh): power steps on I - M_0 in FP32
+// with M_0 from its two leading planes, from a fixed +-1 vector.  ||(I - M_0) v|| for a unit
+// v never exceeds 1 - lambda_min(M_0), so the estimate errs towards a larger lower end (the
+// raw estimate; the steps are steered with half of it).  a_s, b_s: mp floats; zero beyond m.
+__device__ float start_lo_slices(const __half* q, size_t plane, int ld, int m, int mp,
+                                 float* a_s, float* b_s, float* red_s) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float inv_n = rsqrtf((float)m);
   for (int i = tid; i < mp; i += blockDim.x) {
-    a_s[i] = i < m ? (float)S[pos * m + i] : 0.f;       // s_pos (S = S^T)
+    a_s[i] = i < m ? ((i % 3 == 0) ? inv_n : -inv_n) : 0.f;
     b_s[i] = 0.f;
   }
   __syncthreads();
-  float* u = a_s;
-  float* v = b_s;
-  const float sc = (float)c * xscale;
-  for (int t = 0; t < p; ++t) {
-    matvec_slices_f32<3>(q, plane, ld, sc, u, v, m, mp);
-    float* tmp = u; u = v; v = tmp;
+  float nb = 1.f;
+  for (int t = 0; t < kStartLoSteps; ++t) {
+    matvec_slices_f32<2>(q, plane, ld, ldexpf(1.f, E_M - 7), a_s, b_s, m, mp);   // b = M_0 a
+    float part = 0.f;
+    for (int i = tid; i < m; i += blockDim.x) {
+      const float d = a_s[i] - b_s[i];
+      b_s[i] = d;
+      part += d * d;
+    }
+    part = warp_sum_f(part);
+    if (lane == 0) red_s[warp] = part;
+    __syncthreads();
+    float tot = 0.f;
+    for (int w = 0; w < nwarps(); ++w) tot += red_s[w];
+    nb = sqrtf(tot);
+    if (nb == 0.f) return 1.f;      // a lies in M_0's eigenvalue 1 (m = 1): Newton steps
+    if (!(nb > 0.f)) return kLoMin;
+    const float inv = 1.f / nb;
+    for (int i = tid; i < m; i += blockDim.x) a_s[i] = b_s[i] * inv;
+    __syncthreads();
   }
-  float r = 0.f;
-  for (int i = tid; i < m; i += blockDim.x) {
-    const float d = (i == pos ? 1.f : 0.f) - u[i];
-    r += d * d;
-  }
-  r = warp_sum_f(r);
-  if (lane == 0) red_s[warp] = r;
-  __syncthreads();
-  float tot = 0.f;
-  for (int w = 0; w < kWarps; ++w) tot += red_s[w];
-  __syncthreads();
-  return sqrtf(tot);
+  return 1.f - nb;
 }
 
 // ======================================================================================
 // tcgen05 engine
 // ======================================================================================
-constexpr int TC_M = 128, TC_N = 64, TC_K = 32;        // tile and k-slice
+// Output tiles of 128 rows x 48 columns (the last column tile of a row block may be 16 or
+// 32 wide).  Five level accumulators of 48 columns make one 240-column TMEM buffer; two
+// buffers (480 of 512 columns) let the MMAs of tile t+1 run while the epilogue drains t.
+constexpr int TC_M = 128, TC_N = 48, TC_K = 32;        // tile and k-slice
 constexpr int TC_STAGES = 3;
 constexpr int TC_A_PLANE = TC_M * TC_K * 2;            // 8192 B
-constexpr int TC_B_PLANE = TC_N * TC_K * 2;            // 4096 B
-constexpr int TC_STAGE_BYTES = NSL * (TC_A_PLANE + TC_B_PLANE);   // 61440 B
-constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 184320 B
-constexpr uint32_t TC_IDESC = tc::idesc_f16(TC_M, TC_N);
+constexpr int TC_B_PLANE = TC_N * TC_K * 2;            // 3072 B
+constexpr int TC_STAGE_BYTES = NSL * (TC_A_PLANE + TC_B_PLANE);   // 56320 B
+constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 168960 B
+constexpr int TC_BUF_COLS = NSL * TC_N;                // 240 TMEM columns per buffer
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;           // polls before a wait gives up
 constexpr uint32_t TC_TMEM_COLS = 512;
+// tcgen05 CTA: warps 0-7 run the epilogue (warp w: TMEM lane quarter w % 4, column half
+// w / 4 of the tile), warp 8 issues TMA, warp 9 issues MMAs.
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = 320;
+constexpr int TC_TMA_WARP = 8, TC_MMA_WARP = 9;
 
 struct TcState {            // pipeline counters; each role keeps its own copy
   uint32_t pit = 0;         // stages issued (TMA)
@@ -221,28 +269,28 @@ struct TcCtx {
   unsigned char* stages;    // 1024-aligned shared memory
   uint64_t* full;           // [TC_STAGES]
   uint64_t* empty;          // [TC_STAGES]
-  uint64_t* tmem_full;
-  uint64_t* tmem_empty;
+  uint64_t* tmem_full;      // [2]
+  uint64_t* tmem_empty;     // [2]
   int* abort_s;
   uint32_t tmem;
   const CUtensorMap* tm_a;
   const CUtensorMap* tm_b;
 };
 
-// C = A B^T on the tcgen05 engine (see the header comment).  All 256 threads call it.
+// C = A B^T on the tcgen05 engine (see the header comment).  All TC_THREADS threads call it.
 // Returns false if a pipeline wait timed out (the CTA then stops).
-__device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, int epi, Mat Tn,
+__device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y, int flags,
                         const GemmIO& io) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mp = io.mp;
-  const int ntm = (mp + TC_M - 1) / TC_M, ntn = mp / TC_N, KT = mp / TC_K;
+  const int ntm = (mp + TC_M - 1) / TC_M, ntn = (mp + TC_N - 1) / TC_N, KT = mp / TC_K;
   const int ntiles = ntm * ntn;
-  // generic-proxy writes (planes, staging, shared vectors) before async-proxy reads/writes
+  // generic-proxy writes (planes, shared vectors) before async-proxy reads/writes
   tc::fence_proxy_async_global();
   tc::fence_proxy_async_shared();
   __syncthreads();
 
-  if (warp == 0) {
+  if (warp == TC_TMA_WARP) {
     if (lane == 0) {                                   // ---- TMA producer
       for (int t = 0; t < ntiles && !*c.abort_s; ++t) {
         const int tm = t / ntn, tn = t % ntn;
@@ -267,14 +315,20 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, int ep
         }
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == TC_MMA_WARP) {
     if (lane == 0) {                                   // ---- MMA issuer
       for (int t = 0; t < ntiles && !*c.abort_s; ++t) {
-        if (st.tmt > 0 && !tc::mbar_wait(c.tmem_empty, (st.tmt - 1) & 1, TC_WAIT_LIMIT)) {
+        const int tn = t % ntn;
+        const int nw = min(TC_N, mp - tn * TC_N);      // 48, or 16 / 32 for the last tile
+        const uint32_t idesc = tc::idesc_f16(TC_M, nw);
+        const uint32_t b = st.tmt & 1;
+        if (st.tmt >= 2 &&
+            !tc::mbar_wait(&c.tmem_empty[b], ((st.tmt >> 1) - 1) & 1, TC_WAIT_LIMIT)) {
           *c.abort_s = 1;
           break;
         }
         tc::tc_fence_after();
+        const uint32_t d0 = c.tmem + b * TC_BUF_COLS;
         bool ok = true;
         for (int kt = 0; kt < KT; ++kt) {
           const uint32_t s = st.cit % TC_STAGES;
@@ -293,81 +347,80 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, int ep
               for (int sa_i = 0; sa_i <= L; ++sa_i) {
                 const uint64_t da = tc::desc_sw64(sa + sa_i * TC_A_PLANE + kk * 32);
                 const uint64_t db = tc::desc_sw64(sb + (L - sa_i) * TC_B_PLANE + kk * 32);
-                tc::mma_f16(c.tmem + L * TC_N, da, db, TC_IDESC,
-                            (kt | kk | sa_i) != 0 ? 1u : 0u);
+                tc::mma_f16(d0 + L * TC_N, da, db, idesc, (kt | kk | sa_i) != 0 ? 1u : 0u);
               }
             }
           }
-          tc::mma_commit(&c.empty[s]);                 // frees the stage when these finish
+          tc::mma_commit(&c.empty[s]);                 // frees the stage when these MMAs finish
           ++st.cit;
         }
         if (!ok) {
           *c.abort_s = 1;
           break;
         }
-        tc::mma_commit(c.tmem_full);                   // the tile's accumulators are ready
+        tc::mma_commit(&c.tmem_full[b]);               // accumulators of tile t ready
         ++st.tmt;
       }
     }
-  } else if (warp >= 4) {                              // ---- epilogue (TMEM lanes 0..127)
-    const int q4 = warp - 4;
+  } else {                                             // ---- epilogue (TMEM lanes 0..127)
+    const int q4 = warp & 3, half = warp >> 2;
     const float cscale = ldexpf(1.f, A.e + B.e - 14);
     float nrm = 0.f, amax = 0.f;
     for (int t = 0; t < ntiles; ++t) {
-      if (!tc::mbar_wait(c.tmem_full, st.ept & 1, TC_WAIT_LIMIT)) {
+      const uint32_t b = st.ept & 1;
+      if (!tc::mbar_wait(&c.tmem_full[b], (st.ept >> 1) & 1, TC_WAIT_LIMIT)) {
         *c.abort_s = 1;
         break;
       }
       tc::tc_fence_after();
       const int tm = t / ntn, tn = t % ntn;
+      const int nw = min(TC_N, mp - tn * TC_N);
       const int row = tm * TC_M + q4 * 32 + lane;
-      for (int c0 = 0; c0 < TC_N; c0 += 16) {
-        float acc[NSL][16];
+      const uint32_t tbase = c.tmem + ((uint32_t)(q4 * 32) << 16) + b * TC_BUF_COLS;
+      for (int c0 = half * (TC_N / 2); c0 < (half + 1) * (TC_N / 2); c0 += 8) {
+        if (c0 >= nw) break;                           // warp-uniform
+        float acc[NSL][8];
 #pragma unroll
-        for (int L = 0; L < NSL; ++L)
-          tc::tmem_ld16(c.tmem + ((uint32_t)(q4 * 32) << 16) + L * TC_N + c0, acc[L]);
+        for (int L = 0; L < NSL; ++L) tc::tmem_ld8(tbase + L * TC_N + c0, acc[L]);
         tc::tmem_ld_wait();
         if (row < mp) {
-          float vh[16], vl[16];
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const float lv[NSL] = {acc[0][k], acc[1][k], acc[2][k], acc[3][k], acc[4][k]};
-            combine_levels(lv, cscale, vh[k], vl[k]);
-          }
           const int j0 = tn * TC_N + c0;
           const size_t idx0 = (size_t)row * io.ld + j0;
-          store16_slices(C.q, io.plane, idx0, vh, vl, C.e);
-          if (epi == EPI_X) {
+          float yh[8], yl[8], oh[8], ol[8];
+          load8_df(Y.q, io.plane, idx0, Y.e, yh, yl);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) amax = fmaxf(amax, fabsf(vh[k]));
-          } else {
-            if (epi == EPI_M) {
-              float th[16], tl[16];
+          for (int k = 0; k < 8; ++k) {
+            const float lv[NSL] = {acc[0][k], acc[1][k], acc[2][k], acc[3][k], acc[4][k]};
+            float vh, vl;
+            combine_levels(lv, cscale, vh, vl);
+            aff_df(vh, vl, yh[k], yl[k], io.alpha, io.c, oh[k], ol[k]);
+          }
+          store8_slices(C.q, io.plane, idx0, oh, ol, C.e);
+          if (flags & EPI_AMAX) {
 #pragma unroll
-              for (int k = 0; k < 16; ++k) {
-                const int jj = j0 + k;
-                const bool in = (row < io.m) && (jj < io.m);
-                const float d = (row == jj) ? 1.f : 0.f;
-                th[k] = 0.f;
-                tl[k] = 0.f;
-                if (in) t_from_m(vh[k], vl[k], d, io.p, th[k], tl[k]);
-                const float ev = in ? __fadd_rn(__fsub_rn(vh[k], d), vl[k]) : 0.f;
-                nrm += ev * ev;
-              }
-              store16_slices(Tn.q, io.plane, idx0, th, tl, Tn.e);
+            for (int k = 0; k < 8; ++k) amax = fmaxf(amax, fabsf(oh[k]));
+          }
+          if (flags & EPI_NORM) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int jj = j0 + k;
+              const bool in = (row < io.m) && (jj < io.m);
+              const float d = (row == jj) ? 1.f : 0.f;
+              const float ev = in ? __fadd_rn(__fsub_rn(oh[k], d), ol[k]) : 0.f;
+              nrm += ev * ev;
             }
           }
         }
       }
       tc::tc_fence_before();
-      tc::mbar_arrive(c.tmem_empty);
+      tc::mbar_arrive(&c.tmem_empty[b]);
       ++st.ept;
     }
-    if (epi == EPI_M) {
+    if (flags & EPI_NORM) {
       nrm = warp_sum_f(nrm);
       if (lane == 0) atomicAdd(io.norm2_s, nrm);
     }
-    if (epi == EPI_X) {
+    if (flags & EPI_AMAX) {
       for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
       if (lane == 0) atomicMax(io.amax_s, __float_as_uint(amax));
     }
@@ -423,7 +476,7 @@ __device__ __forceinline__ void mma16816(float* c, const uint32_t* a, const uint
 
 // C = A B (mp x mp, sliced, row-major ld).  All eight warps work on one 64 x 64 output tile
 // at a time (warps 2 x 4, 32 x 16 each), 3-stage cp.async pipeline over k.
-__device__ void gemm_sync(Mat A, Mat B, Mat C, int epi, Mat Tn, const GemmIO& io,
+__device__ void gemm_sync(Mat A, Mat B, Mat C, Mat Y, int flags, const GemmIO& io,
                           __half* smem) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -526,30 +579,26 @@ __device__ void gemm_sync(Mat A, Mat B, Mat C, int epi, Mat Tn, const GemmIO& io
             const int jj = j0 + wn * 16 + n * 8 + 2 * q + c2;
             const float lv[NSL] = {acc[0][mt][n][ci], acc[1][mt][n][ci], acc[2][mt][n][ci],
                                    acc[3][mt][n][ci], acc[4][mt][n][ci]};
-            float vh, vl;
+            float vh, vl, yh, yl, oh, ol;
             combine_levels(lv, cscale, vh, vl);
             const size_t idx = (size_t)i * ld + jj;
-            put_slices(C.q, plane, idx, vh, vl, C.e);
-            if (epi == EPI_X) {
-              amax = fmaxf(amax, fabsf(vh));
-            } else {
-              if (epi == EPI_M) {
-                const bool in = (i < io.m) && (jj < io.m);
-                const float d = (i == jj) ? 1.f : 0.f;
-                float th = 0.f, tl = 0.f;
-                if (in) t_from_m(vh, vl, d, io.p, th, tl);
-                put_slices(Tn.q, plane, idx, th, tl, Tn.e);
-                const float ev = in ? __fadd_rn(__fsub_rn(vh, d), vl) : 0.f;
-                nrm += ev * ev;
-              }
+            load1_df(Y.q, plane, idx, Y.e, yh, yl);
+            aff_df(vh, vl, yh, yl, io.alpha, io.c, oh, ol);
+            put_slices(C.q, plane, idx, oh, ol, C.e);
+            if (flags & EPI_AMAX) amax = fmaxf(amax, fabsf(oh));
+            if (flags & EPI_NORM) {
+              const bool in = (i < io.m) && (jj < io.m);
+              const float d = (i == jj) ? 1.f : 0.f;
+              const float ev = in ? __fadd_rn(__fsub_rn(oh, d), ol) : 0.f;
+              nrm += ev * ev;
             }
           }
   }
-  if (epi == EPI_M) {
+  if (flags & EPI_NORM) {
     nrm = warp_sum_f(nrm);
     if (lane == 0) atomicAdd(io.norm2_s, nrm);
   }
-  if (epi == EPI_X) {
+  if (flags & EPI_AMAX) {
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     if (lane == 0) atomicMax(io.amax_s, __float_as_uint(amax));
   }
@@ -565,26 +614,27 @@ constexpr size_t kSmemTail = 256;                       // barriers and flags
 template <bool TC>
 __host__ __device__ constexpr size_t stage_area() { return TC ? (size_t)TC_STAGE_AREA : (size_t)SY_STAGE_AREA; }
 // vectors used between GEMMs alias the stage area
-constexpr size_t kVecBytes = 3 * SUBMAT_MAX_M * sizeof(double) + 2 * kWarps * sizeof(double) +
+constexpr size_t kVecBytes = 4 * SUBMAT_MAX_M * sizeof(double) + kRedDoubles * sizeof(double) +
                              SUBMAT_MAX_M * sizeof(int32_t);
 static_assert(kVecBytes <= (size_t)SY_STAGE_AREA, "vector area must fit in the stage area");
 
 template <bool TC>
-__global__ void __launch_bounds__(kThreads, 1) fwd_mixed_kernel(const __grid_constant__ FwdArgs a) {
+__global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
+    fwd_mixed_kernel(const __grid_constant__ FwdArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   double* y_s = reinterpret_cast<double*>(sm);
   double* v_s = y_s + SUBMAT_MAX_M;
   double* w_s = v_s + SUBMAT_MAX_M;
-  double* red_s = w_s + SUBMAT_MAX_M;                 // 2*kWarps doubles
-  int32_t* R_s = reinterpret_cast<int32_t*>(red_s + 2 * kWarps);
+  double* red_s = w_s + SUBMAT_MAX_M;                 // kRedDoubles doubles
+  int32_t* R_s = reinterpret_cast<int32_t*>(red_s + kRedDoubles);
   unsigned char* tail = sm + stage_area<TC>();
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tail);  // full[3], empty[3], tmem_full, tmem_empty
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tail + 64);
-  int* abort_s = reinterpret_cast<int*>(tail + 68);
-  float* norm2_s = reinterpret_cast<float*>(tail + 72);
-  unsigned* amax_s = reinterpret_cast<unsigned*>(tail + 76);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tail);  // full[3] empty[3] tmem_full[2] tmem_empty[2]
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tail + 96);
+  int* abort_s = reinterpret_cast<int*>(tail + 100);
+  float* norm2_s = reinterpret_cast<float*>(tail + 104);
+  unsigned* amax_s = reinterpret_cast<unsigned*>(tail + 108);
   __shared__ int job_s;
 
   const int tid = threadIdx.x;
@@ -599,8 +649,9 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_mixed_kernel(const __grid_con
   TcState tst;
   if (TC) {
     if (tid == 0) {
-      for (int i = 0; i < 2 * TC_STAGES + 1; ++i) tc::mbar_init(&bars[i], 1);
-      tc::mbar_init(&bars[2 * TC_STAGES + 1], 128);
+      for (int i = 0; i < 2 * TC_STAGES + 2; ++i) tc::mbar_init(&bars[i], 1);
+      tc::mbar_init(&bars[2 * TC_STAGES + 2], TC_EPI_WARPS * 32);
+      tc::mbar_init(&bars[2 * TC_STAGES + 3], TC_EPI_WARPS * 32);
       *abort_s = 0;
       tc::fence_mbar_init();
     }
@@ -612,7 +663,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_mixed_kernel(const __grid_con
     tcx.full = bars;
     tcx.empty = bars + TC_STAGES;
     tcx.tmem_full = bars + 2 * TC_STAGES;
-    tcx.tmem_empty = bars + 2 * TC_STAGES + 1;
+    tcx.tmem_empty = bars + 2 * TC_STAGES + 2;
     tcx.abort_s = abort_s;
     tcx.tmem = *tmem_holder;
     tcx.tm_a = &a.tm_a;
@@ -634,123 +685,219 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_mixed_kernel(const __grid_con
     const int p = a.p;
     const int mp = pad_mixed(m);
 
-    Mat X[2] = {{hb + 0 * NSL * plane, E_T, plane_base + 0}, {hb + 1 * NSL * plane, E_T, plane_base + 5}};
-    Mat T[2] = {{hb + 2 * NSL * plane, E_T, plane_base + 10}, {hb + 3 * NSL * plane, E_T, plane_base + 15}};
-    Mat M[2] = {{hb + 4 * NSL * plane, E_M, plane_base + 20}, {hb + 5 * NSL * plane, E_M, plane_base + 25}};
+    // Two X buffers (p = 1 only) and three buffers for M_k and the partial products T^s M_k
+    // (M_k is the A operand of all p products of an iteration and stays in place).
+    Mat X[2] = {{hb + 0 * NSL * plane, 0, plane_base + 0}, {hb + 1 * NSL * plane, 0, plane_base + 5}};
+    Mat B3[3] = {{hb + 2 * NSL * plane, E_M, plane_base + 10},
+                 {hb + 3 * NSL * plane, E_M, plane_base + 15},
+                 {hb + 4 * NSL * plane, E_M, plane_base + 20}};
+    double* yg = reinterpret_cast<double*>(hb + 34 * plane);     // tracked X_k e_pos (FP64)
+    float* ug = reinterpret_cast<float*>(yg + SUBMAT_MAX_M);     // tracked residual vector
 
     const double lam = gather_submatrix(a.rowptr, a.colind, a.vals_in, j, m, R_s, S, red_s);
     const double inv_lam = 1.0 / lam;
 
-    // M_0 = S / lambda_bar, T_0 = ((p+1) I - M_0)/p, X_1 = X_0 T_0 = T_0 (leading mp x mp),
-    // eight consecutive columns per thread; one FP64 product and one FP64 difference per
-    // entry, the rest in double-float FP32.
+    // M_0 = S / lambda_bar (leading mp x mp, eight consecutive columns per thread), in
+    // double-float FP32 from the integer split of the FP64 values; also ||M_0 - I||_F^2.
     const int mp8 = mp / 8;
-    for (int e = tid; e < mp * mp8; e += blockDim.x) {
-      const int i = e / mp8, j0 = (e % mp8) * 8;
-      float mh[8], ml[8], th[8], tl[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int jj = j0 + c;
-        mh[c] = ml[c] = th[c] = tl[c] = 0.f;
-        if (i < m && jj < m) {
-          const double mv = S[i * m + jj] * inv_lam;
-          mh[c] = (float)mv;
-          ml[c] = (float)(mv - (double)mh[c]);
-          t_from_m(mh[c], ml[c], i == jj ? 1.f : 0.f, p, th[c], tl[c]);
-        }
-      }
-      const size_t g = (size_t)i * LD + j0;
-      store8_slices(M[0].q, plane, g, mh, ml, E_M);
-      store8_slices(T[0].q, plane, g, th, tl, E_T);
-      store8_slices(X[0].q, plane, g, th, tl, E_T);
-    }
+    float ih, il;
+    split_dbl(inv_lam, ih, il);
     if (tid == 0) *norm2_s = 0.f;
+    __syncthreads();
+    {
+      float nrm = 0.f;
+      for (int e = tid; e < mp * mp8; e += blockDim.x) {
+        const int i = e / mp8, j0 = (e % mp8) * 8;
+        float mh[8], ml[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int jj = j0 + c;
+          mh[c] = ml[c] = 0.f;
+          if (i < m && jj < m) {
+            float sh, sl;
+            split_dbl(S[i * m + jj], sh, sl);
+            mul_df(sh, sl, ih, il, mh[c], ml[c]);
+            const float ev = __fadd_rn(__fsub_rn(mh[c], i == jj ? 1.f : 0.f), ml[c]);
+            nrm += ev * ev;
+          }
+        }
+        store8_slices(B3[0].q, plane, (size_t)i * LD + j0, mh, ml, E_M);
+      }
+      nrm = warp_sum_f(nrm);
+      if ((tid & 31) == 0) atomicAdd(norm2_s, nrm);
+    }
+    __syncthreads();
+    float nrm2 = *norm2_s;
+
+    // lower end of M_0's spectrum: the raw estimate gives the condition estimate
+    // lambda_bar / lambda_min(S) = 1 / lambda_min(M_0), half of it steers the steps
+    const float lo_raw = start_lo_slices(B3[0].q, plane, LD, m, mp, reinterpret_cast<float*>(v_s),
+                                         reinterpret_cast<float*>(w_s),
+                                         reinterpret_cast<float*>(red_s));
+    float lo = 0.5f * lo_raw;
+
+    // tracked vectors (p >= 2): y_0 = e_pos, u_0 = M_0 e_pos
+    const bool track = (p >= 2);
+    if (track) {
+      for (int i = tid; i < m; i += blockDim.x) {
+        yg[i] = (i == pos) ? 1.0 : 0.0;
+        ug[i] = (float)(S[pos * m + i] * inv_lam);
+      }
+    }
     __threadfence();             // planes are read next through L2 (cp.async.cg / TMA)
     __syncthreads();
 
-    GemmIO io{mp, m, p, LD, plane, norm2_s, amax_s};
-    auto gemm = [&](Mat A, Mat B, Mat C, int epi, Mat Tn) -> bool {
-      if (TC) return gemm_tc(tcx, tst, A, B, C, epi, Tn, io);
-      gemm_sync(A, B, C, epi, Tn, io, reinterpret_cast<__half*>(sm));
+    GemmIO io{mp, m, p, LD, plane, norm2_s, amax_s, 0.f, 0.f};
+    auto gemm = [&](Mat A, Mat B, Mat C, Mat Y, int flags) -> bool {
+      if (TC) return gemm_tc(tcx, tst, A, B, C, Y, flags, io);
+      gemm_sync(A, B, C, Y, flags, io, reinterpret_cast<__half*>(sm));
       return true;
     };
 
-    int xc = 0, tc_i = 0, mc = 0;
+    // y <- c (alpha y - M y) in FP64 / double-float, u <- (c (alpha I - M))^p u in FP32:
+    // the step T = c (alpha I - M) applied to the tracked column and residual vectors.
+    float* yh_s = reinterpret_cast<float*>(v_s);                 // 2 x SUBMAT_MAX_M floats
+    float* yl_s = yh_s + SUBMAT_MAX_M;
+    float* u_s = reinterpret_cast<float*>(w_s);
+    float* t_s = u_s + SUBMAT_MAX_M;
+    double* my_s = reinterpret_cast<double*>(R_s + SUBMAT_MAX_M);
+    auto vec_step = [&](const Mat& Mk, double c, double alpha) {
+      for (int i = tid; i < mp; i += blockDim.x) {
+        const double yv = i < m ? yg[i] : 0.0;
+        y_s[i] = yv;
+        float h, l;
+        split_dbl(yv, h, l);
+        yh_s[i] = h;
+        yl_s[i] = l;
+        u_s[i] = i < m ? ug[i] : 0.f;
+        t_s[i] = 0.f;
+      }
+      __syncthreads();
+      matvec_slices_df(Mk.q, plane, LD, Mk.e, yh_s, yl_s, my_s, m, mp);
+      for (int i = tid; i < m; i += blockDim.x) yg[i] = c * (alpha * y_s[i] - my_s[i]);
+      const float cf = (float)c, af = (float)alpha;
+      for (int t = 0; t < p; ++t) {
+        matvec_slices_f32<3>(Mk.q, plane, LD, ldexpf(1.f, Mk.e - 7), u_s, t_s, m, mp);
+        for (int i = tid; i < m; i += blockDim.x) u_s[i] = cf * (af * u_s[i] - t_s[i]);
+        __syncthreads();
+      }
+      for (int i = tid; i < m; i += blockDim.x) ug[i] = u_s[i];
+      __syncthreads();
+    };
+
+    int xc = 0, mi = 0;
     int n_gemm = 0;
     const float tol2 = (float)(a.tol * a.tol * (double)m);
     const float stag2 = 1e-4f * (float)m;       // (1e-2)^2 m
-    int iters = 1;
-    float nrm2 = 0.f, prev2 = 3.0e38f;
-    bool bad = false, stop = false;
+    int iters = 0;
+    float prev2 = 3.0e38f, xmax = 1.f;
+    bool bad = !(nrm2 == nrm2), stop = false;
 
-    // X_{k+1} = X_k T_k, sliced directly with a predicted exponent: X_k and T_k are SPD and
-    // commute, and T_k <= (p+1)/p I, so X_{k+1} <= (p+1)/p X_k in the Loewner order and the
-    // largest entry (a diagonal one) grows at most by (p+1)/p.  The epilogue measures the
-    // new largest entry for the next prediction.
-    float xmax = (float)(p + 1) / (float)p;      // |X_1| = |T_0| <= (p+1)/p
-    auto x_update = [&]() -> bool {
-      X[xc ^ 1].e = exp_bound(xmax * ((float)(p + 1) / (float)p) * (1.f + 1e-6f));
-      if (tid == 0) *amax_s = 0u;
-      __syncthreads();
-      if (!gemm(X[xc], T[tc_i], X[xc ^ 1], EPI_X, T[tc_i])) return false;
-      xmax = __uint_as_float(*amax_s);
-      xc ^= 1;
-      ++n_gemm;
-      return true;
-    };
-
-    for (;;) {
-      // M <- T^p M, the last product also writes T_next and ||M - I||_F^2
-      Mat cur = M[mc];
-      int free_slot = mc ^ 1;
-      for (int s = 1; s <= p && !stop; ++s) {
+    // Iteration k: T_k = c_k (alpha_k I - M_k) with constants for the interval
+    // [max(lo_k, 1 - ||M_k - I||_F), 1] (the Frobenius norm bounds the distance of every
+    // eigenvalue from 1); X_{k+1} = X_k T_k (tracked as vectors for p >= 2, a product for
+    // p = 1), M_{k+1} = T_k^p M_k as p products with M_k as the A operand.
+    while (!bad) {
+      const ScaledStep st = scaled_step(fmaxf(lo, 1.f - sqrtf(nrm2)), p);
+      io.c = st.c;
+      io.alpha = st.alpha;
+      const Mat Mk = B3[mi];
+      if (track) {
+        vec_step(Mk, (double)st.c, (double)st.alpha);
+      } else if (iters == 0) {
+        // X_1 = T_0 (elementwise from M_0)
+        X[0].e = exp_of(st.tmax);
+        xmax = st.tmax;
+        for (int e = tid; e < mp * mp8; e += blockDim.x) {
+          const int i = e / mp8, j0 = (e % mp8) * 8;
+          const size_t g = (size_t)i * LD + j0;
+          float vh[8], vl[8], th[8], tl[8];
+          load8_df(Mk.q, plane, g, Mk.e, vh, vl);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            th[c] = tl[c] = 0.f;
+            if (i < m && j0 + c < m)
+              t_affine(vh[c], vl[c], i == j0 + c ? 1.f : 0.f, st.alpha, 0.f, st.c, 0.f, th[c],
+                       tl[c]);
+          }
+          store8_slices(X[0].q, plane, g, th, tl, X[0].e);
+        }
+        __threadfence();
+        __syncthreads();
+      } else {
+        // X_{k+1} = c (alpha X_k - X_k M_k); X_k, T_k SPD and commuting with T_k <= tmax I,
+        // so the largest entry (a diagonal one) grows at most by tmax
+        X[xc ^ 1].e = exp_of(xmax * st.tmax);
+        if (tid == 0) *amax_s = 0u;
+        __syncthreads();
+        if (!gemm(X[xc], Mk, X[xc ^ 1], X[xc], EPI_AMAX)) { stop = true; break; }
+        ++n_gemm;
+        xmax = __uint_as_float(*amax_s);
+        xc ^= 1;
+      }
+      // M_{k+1} = T_k^p M_k: P_s = c (alpha P_{s-1} - M_k P_{s-1}), P_0 = M_k
+      int src = mi, dst = (mi + 1) % 3;
+      for (int s = 1; s <= p; ++s) {
         const bool last = (s == p);
-        M[free_slot].e = last ? E_M : E_P;
-        Mat dst = M[free_slot];
+        B3[dst].e = last ? E_M : exp_of(partial_bound(st, s));
         if (last) {
           if (tid == 0) *norm2_s = 0.f;
           __syncthreads();
         }
-        if (!gemm(T[tc_i], cur, dst, last ? EPI_M : EPI_FIXED, T[tc_i ^ 1])) stop = true;
+        if (!gemm(Mk, B3[src], B3[dst], B3[src], last ? EPI_NORM : 0)) { stop = true; break; }
         ++n_gemm;
-        cur = dst;
-        mc = free_slot;
-        free_slot ^= 1;
+        src = dst;
+        dst = 3 - mi - dst;                     // the buffer that is neither M_k nor P_s
       }
       if (stop) break;
-      tc_i ^= 1;
+      mi = src;
+      lo = st.lo_next;
+      ++iters;
       nrm2 = *norm2_s;
       __syncthreads();
       if (!(nrm2 == nrm2) || nrm2 > 1e30f) { bad = true; break; }
       if (nrm2 <= tol2 || iters >= a.k_max) break;
       if (nrm2 <= stag2 && nrm2 > 0.25f * prev2) break;     // at the rounding-error floor
       prev2 = nrm2;
-      if (!x_update()) { stop = true; break; }
-      ++iters;
     }
     if (stop) break;
-    if (!bad && !x_update()) break;
 
+    // last step: Newton's T = ((p+1) I - M)/p, whose first-order part is M^(-1/p)
     double resid = 1e300;
     float kest = 0.f;
-    if (!bad) {
-      const double c = pow(lam, -1.0 / (double)p);
+    const double c = pow(lam, -1.0 / (double)p);
+    if (!bad && track) {
+      vec_step(B3[mi], 1.0 / (double)p, (double)(p + 1));
+      // column pos of F = c X and the residual F^p s_pos - e_pos = u - e_pos
+      float r = 0.f;
+      for (int i = tid; i < m; i += blockDim.x) {
+        y_s[i] = c * yg[i];
+        const float d = ug[i] - (i == pos ? 1.f : 0.f);
+        r += d * d;
+      }
+      r = warp_sum_f(r);
+      if ((tid & 31) == 0) reinterpret_cast<float*>(red_s)[tid >> 5] = r;
+      __syncthreads();
+      float tot = 0.f;
+      for (int w = 0; w < nwarps(); ++w) tot += reinterpret_cast<float*>(red_s)[w];
+      __syncthreads();
+      resid = sqrt((double)tot);
+      kest = lo_raw > 0.f ? 1.f / lo_raw : 3.0e38f;
+    } else if (!bad) {
+      io.c = 1.f;                                // p = 1: X (2 I - M)
+      io.alpha = 2.f;
+      X[xc ^ 1].e = exp_of(xmax * 2.f);
+      if (tid == 0) *amax_s = 0u;
+      __syncthreads();
+      if (!gemm(X[xc], B3[mi], X[xc ^ 1], X[xc], EPI_AMAX)) break;
+      ++n_gemm;
+      xc ^= 1;
       SliceLoad xl{X[xc].q, plane, LD, ldexp(1.0, X[xc].e - 7)};
       const float xs = ldexpf(1.f, X[xc].e - 7);
-      if (p >= 2 && a.refine_steps < 1) {
-        for (int i = tid; i < m; i += blockDim.x) y_s[i] = c * xl(i, pos);
-        resid = column_residual_f32(X[xc].q, plane, LD, xs, c, S, m, mp, pos, p,
-                                    reinterpret_cast<float*>(v_s), reinterpret_cast<float*>(w_s),
-                                    reinterpret_cast<float*>(red_s));
-      } else {
-        resid = refine_column(xl, c, S, m, pos, p, a.refine_steps, y_s, v_s, w_s, red_s);
-      }
-      // condition estimate lambda_bar / lambda_min = lambda_max(X)^p (X ~ (S/lambda_bar)^(-1/p))
-      const float lx = power_max_slices(X[xc].q, plane, LD, xs, m, mp,
-                                        reinterpret_cast<float*>(v_s),
-                                        reinterpret_cast<float*>(w_s),
-                                        reinterpret_cast<float*>(red_s), 6);
-      kest = powf(lx, (float)p);
+      resid = refine_column(xl, c, S, m, pos, p, a.refine_steps, y_s, v_s, w_s, red_s);
+      // condition estimate lambda_bar / lambda_min = lambda_max(X) (X ~ (S/lambda_bar)^(-1))
+      kest = power_max_slices(X[xc].q, plane, LD, xs, m, mp, reinterpret_cast<float*>(v_s),
+                              reinterpret_cast<float*>(w_s), reinterpret_cast<float*>(red_s), 6);
     }
     const bool illcond = !bad && !(kest <= (float)a.kappa_max);
     const bool ok = !bad && (resid <= a.resid_tol) && !illcond;
@@ -798,7 +945,7 @@ cudaError_t launch_fwd_mixed(const FwdArgs& a, int grid, cudaStream_t s) {
   if (a.engine == 1)
     fwd_mixed_kernel<false><<<grid, kThreads, smem_bytes<false>(), s>>>(a);
   else
-    fwd_mixed_kernel<true><<<grid, kThreads, smem_bytes<true>(), s>>>(a);
+    fwd_mixed_kernel<true><<<grid, TC_THREADS, smem_bytes<true>(), s>>>(a);
   return cudaGetLastError();
 }
 

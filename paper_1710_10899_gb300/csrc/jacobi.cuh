@@ -30,10 +30,10 @@ static __device__ int jacobi_eig(double* __restrict__ A, double* __restrict__ V,
     }
     off = warp_sum(off);
     tot = warp_sum(tot);
-    if (lane == 0) { red_s[warp] = off; red_s[kWarps + warp] = tot; }
+    if (lane == 0) { red_s[warp] = off; red_s[kMaxWarps + warp] = tot; }
     __syncthreads();
     double so = 0.0, st = 0.0;
-    for (int w = 0; w < kWarps; ++w) { so += red_s[w]; st += red_s[kWarps + w]; }
+    for (int w = 0; w < nwarps(); ++w) { so += red_s[w]; st += red_s[kMaxWarps + w]; }
     __syncthreads();
     if (!(st <= 1.7e308)) return -1;     // NaN or infinity somewhere in A
     if (m == 1 || !(so > 1e-28 * st)) break;       // off(A) <= 1e-14 ||A||_F

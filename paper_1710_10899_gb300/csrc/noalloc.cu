@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(kThreads, 1) noalloc_fp64_kernel(NoallocArgs a
   double* y_s = gsm + 2 * fp64::TK * fp64::TB;
   double* v_s = y_s + SUBMAT_MAX_M;
   double* w_s = v_s + SUBMAT_MAX_M;
-  double* red_s = w_s + SUBMAT_MAX_M;                                // 2*kWarps
-  double* norm2_s = red_s + 2 * kWarps;
+  double* red_s = w_s + SUBMAT_MAX_M;                                // kRedDoubles
+  double* norm2_s = red_s + kRedDoubles;
   int32_t* R_s = reinterpret_cast<int32_t*>(norm2_s + 2);          // SUBMAT_MAX_M
   int32_t* pair_s = R_s + SUBMAT_MAX_M;                              // SUBMAT_MAX_M
   __shared__ int job_s, bad_s;
@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(kThreads, 1) noalloc_fp64_kernel(NoallocArgs a
           if (tid == 0) *norm2_s = 0.0;
           __syncthreads();
         }
-        fp64::gemm64(T[tc], cur, dst, mp, m, last ? fp64::EPI_M : fp64::EPI_STORE, T[tc ^ 1], p,
-                     gsm, norm2_s);
+        fp64::gemm64(T[tc], cur, dst, mp, m, last ? fp64::EPI_M : fp64::EPI_STORE, T[tc ^ 1], 1.0,
+                     (double)(p + 1), (double)p, gsm, norm2_s);   // Newton's step
         cur = dst;
         mc = free_slot;
         free_slot ^= 1;
@@ -144,13 +144,15 @@ __global__ void __launch_bounds__(kThreads, 1) noalloc_fp64_kernel(NoallocArgs a
       if (nrm2 <= tol2 || iters >= 40) break;
       if (nrm2 <= stag2 && nrm2 > 0.25 * prev2) break;
       prev2 = nrm2;
-      fp64::gemm64(X[xc], T[tc], X[xc ^ 1], mp, m, fp64::EPI_STORE, nullptr, p, gsm, norm2_s);
+      fp64::gemm64(X[xc], T[tc], X[xc ^ 1], mp, m, fp64::EPI_STORE, nullptr, 0.0, 0.0, 1.0, gsm,
+                   norm2_s);
       xc ^= 1;
       ++iters;
     }
     double resid = 1e300;
     if (!bad) {
-      fp64::gemm64(X[xc], T[tc], X[xc ^ 1], mp, m, fp64::EPI_STORE, nullptr, p, gsm, norm2_s);
+      fp64::gemm64(X[xc], T[tc], X[xc ^ 1], mp, m, fp64::EPI_STORE, nullptr, 0.0, 0.0, 1.0, gsm,
+                   norm2_s);
       xc ^= 1;
       DenseLoad xl{X[xc], mp};
       resid = refine_column(xl, pow(lam, -1.0 / (double)p), S, m, pos, p, p == 1 ? 2 : 0,
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) noalloc_fp64_kernel(NoallocArgs a
 }
 
 size_t smem_noalloc() {
-  return (2 * fp64::TK * fp64::TB + 3 * SUBMAT_MAX_M + 2 * kWarps + 2) * sizeof(double) +
+  return (2 * fp64::TK * fp64::TB + 3 * SUBMAT_MAX_M + kRedDoubles + 2) * sizeof(double) +
          2 * SUBMAT_MAX_M * sizeof(int32_t);
 }
 

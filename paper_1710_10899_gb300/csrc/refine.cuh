@@ -21,7 +21,7 @@ template <class FLoad>
 __device__ __forceinline__ void matvec_rows(const FLoad& F, double c, const double* in,
                                             double* out, int m) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = warp; i < m; i += kWarps) {
+  for (int i = warp; i < m; i += nwarps()) {
     double s = 0.0;
     for (int k = lane; k < m; k += 32) s = fma(F(i, k), in[k], s);
     s = warp_sum(s);
@@ -38,7 +38,7 @@ __device__ __forceinline__ double block_norm2(const double* v, int m, double* re
   if (lane == 0) red_s[warp] = s;
   __syncthreads();
   double t = 0.0;
-  for (int w = 0; w < kWarps; ++w) t += red_s[w];
+  for (int w = 0; w < nwarps(); ++w) t += red_s[w];
   __syncthreads();
   return sqrt(t);
 }
@@ -112,7 +112,7 @@ __device__ float power_max_eig(const XLoad& X, int m, float* a_s, float* b_s, fl
   __syncthreads();
   float lam = 0.f;
   for (int it = 0; it < iters; ++it) {
-    for (int i = warp; i < m; i += kWarps) {
+    for (int i = warp; i < m; i += nwarps()) {
       float s = 0.f;
       for (int k = lane; k < m; k += 32) s = fmaf((float)X(i, k), a_s[k], s);
       s = warp_sum_f(s);
@@ -123,10 +123,10 @@ __device__ float power_max_eig(const XLoad& X, int m, float* a_s, float* b_s, fl
     for (int i = tid; i < m; i += blockDim.x) { na += a_s[i] * a_s[i]; nb += b_s[i] * b_s[i]; }
     na = warp_sum_f(na);
     nb = warp_sum_f(nb);
-    if (lane == 0) { red_s[warp] = na; red_s[kWarps + warp] = nb; }
+    if (lane == 0) { red_s[warp] = na; red_s[kMaxWarps + warp] = nb; }
     __syncthreads();
     float ta = 0.f, tb = 0.f;
-    for (int w = 0; w < kWarps; ++w) { ta += red_s[w]; tb += red_s[kWarps + w]; }
+    for (int w = 0; w < nwarps(); ++w) { ta += red_s[w]; tb += red_s[kMaxWarps + w]; }
     lam = sqrtf(tb / ta);
     const float inv = tb > 0.f ? rsqrtf(tb) : 0.f;
     for (int i = tid; i < m; i += blockDim.x) a_s[i] = b_s[i] * inv;

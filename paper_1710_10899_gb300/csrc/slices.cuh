@@ -72,6 +72,95 @@ __device__ __forceinline__ void t_from_m(float vh, float vl, float d, int p, flo
   tl = __fadd_rn(rem, a2) * pinv;
 }
 
+// c (alpha d - v) for v = vh + vl, in double-float, with c = ch + cl and alpha = ah + al
+// (the step matrix of a scaled step; d is 1 on the diagonal, else 0).
+__device__ __forceinline__ void t_affine(float vh, float vl, float d, float ah, float al,
+                                         float ch, float cl, float& th, float& tl) {
+  float a1, a2;
+  two_sum(ah * d, -vh, a1, a2);                     // ah * d is exact
+  a2 = __fadd_rn(a2, __fsub_rn(al * d, vl));
+  two_sum(a1, a2, a1, a2);
+  const float h = __fmul_rn(a1, ch);
+  const float err = __fmaf_rn(a1, ch, -h);          // a1 * ch - h exactly
+  const float l = __fadd_rn(err, __fadd_rn(__fmul_rn(a1, cl), __fmul_rn(a2, ch)));
+  two_sum(h, l, th, tl);
+}
+
+// Double-float split of a double by integer operations (FP64 units are scarce): h takes the
+// leading 24 significant bits, l the next 29 rounded to 24, so h + l keeps about 48 bits.
+// Magnitudes outside [2^-74, 2^100] are not expected here; they keep only h (or 0).
+__device__ __forceinline__ void split_dbl(double v, float& h, float& l) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  if (ex < 1023 - 74 || ex > 1023 + 100) {
+    h = ex < 1023 - 74 ? 0.f : __int_as_float((int)(sign | 0x7F800000u));
+    l = 0.f;
+    return;
+  }
+  const unsigned long long frac = b & ((1ull << 52) - 1);
+  h = __int_as_float((int)(sign | ((unsigned)(ex - 1023 + 127) << 23) | (unsigned)(frac >> 29)));
+  const float r = __uint2float_rn((unsigned)(frac & ((1u << 29) - 1)));       // < 2^29
+  const float sc = __int_as_float((int)(((unsigned)(ex - 1075 + 127)) << 23));   // 2^(ex-1075)
+  l = __int_as_float(__float_as_int(r * sc) | (int)sign);
+}
+
+// (ah + al) (bh + bl) as a double-float.
+__device__ __forceinline__ void mul_df(float ah, float al, float bh, float bl, float& h,
+                                       float& l) {
+  const float p = __fmul_rn(ah, bh);
+  const float e = __fmaf_rn(ah, bh, -p);
+  two_sum(p, __fadd_rn(e, __fadd_rn(__fmul_rn(ah, bl), __fmul_rn(al, bh))), h, l);
+}
+
+// Eight consecutive values of a sliced matrix (scale exponent e) as double-floats.  The
+// planes' integers recombine exactly: q0 2^8 + q1 < 2^16 and q2 2^16 + q3 2^8 + q4 < 2^24.
+__device__ __forceinline__ void load8_df(const __half* q, size_t plane, size_t idx0, int e,
+                                         float* vh, float* vl) {
+  uint4 raw[NSL];
+#pragma unroll
+  for (int k = 0; k < NSL; ++k) raw[k] = *reinterpret_cast<const uint4*>(q + k * plane + idx0);
+  const float sc = ldexpf(1.f, e - 7);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float qq[NSL];
+#pragma unroll
+    for (int k = 0; k < NSL; ++k) qq[k] = __half2float(reinterpret_cast<const __half*>(&raw[k])[c]);
+    const float a = __fmaf_rn(qq[0], 256.f, qq[1]);
+    const float b = __fmaf_rn(qq[2], 65536.f, __fmaf_rn(qq[3], 256.f, qq[4]));
+    float h, l;
+    two_sum(a * (1.f / 256.f), b * (1.f / 4294967296.f), h, l);
+    vh[c] = h * sc;
+    vl[c] = l * sc;
+  }
+}
+
+// c (alpha y - v) for y = yh + yl and v = vh + vl, in double-float (c, alpha exact FP32).
+__device__ __forceinline__ void aff_df(float vh, float vl, float yh, float yl, float alpha,
+                                       float c, float& oh, float& ol) {
+  float ah, al, s, e;
+  mul_df(yh, yl, alpha, 0.f, ah, al);
+  two_sum(ah, -vh, s, e);
+  e = __fadd_rn(e, __fsub_rn(al, vl));
+  two_sum(s, e, s, e);
+  mul_df(s, e, c, 0.f, oh, ol);
+}
+
+// One value of a sliced matrix (scale exponent e) as a double-float (see load8_df).
+__device__ __forceinline__ void load1_df(const __half* q, size_t plane, size_t idx, int e,
+                                         float& vh, float& vl) {
+  float qq[NSL];
+#pragma unroll
+  for (int k = 0; k < NSL; ++k) qq[k] = __half2float(q[k * plane + idx]);
+  const float a = __fmaf_rn(qq[0], 256.f, qq[1]);
+  const float b = __fmaf_rn(qq[2], 65536.f, __fmaf_rn(qq[3], 256.f, qq[4]));
+  const float sc = ldexpf(1.f, e - 7);
+  float h, l;
+  two_sum(a * (1.f / 256.f), b * (1.f / 4294967296.f), h, l);
+  vh = h * sc;
+  vl = l * sc;
+}
+
 // Exponent e with |v| <= 2^e for the largest magnitude amax (at least -60).
 __device__ __forceinline__ int exp_bound(float amax) {
   if (!(amax > 0.f)) return -60;
