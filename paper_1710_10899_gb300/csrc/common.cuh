@@ -136,9 +136,24 @@ __device__ __forceinline__ int find_sorted(const int32_t* a, int len, int32_t ke
   return -1;
 }
 
+// |v| of a double as a float from its leading bits (integer operations only: FP64 units are
+// scarce); relative error below 2^-20, NaN stays NaN, magnitudes beyond the float range give
+// 0 or inf.
+__device__ __forceinline__ float abs_f32_approx(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v) & 0x7FFFFFFFu;
+  const int ex = (int)(hi >> 20);
+  if (ex == 0x7FF) return __int_as_float(0x7FC00000);
+  if (ex <= 1023 - 127) return 0.f;
+  if (ex >= 1023 + 128) return __int_as_float(0x7F800000);
+  return __int_as_float((int)(((unsigned)(ex - 1023 + 127) << 23) | ((hi & 0xFFFFFu) << 3)));
+}
+
 // Algorithm 1 for row j (value part): S[k*m + l] = A[R[k]][R[l]] in FP64 (zero where not
 // stored), R staged in shared memory (R_s, m ints), and the Gershgorin bound
-// max_k sum_l |S_kl| returned to every thread.  red_s: kRedDoubles doubles of shared memory.
+// max_k sum_l |S_kl| returned to every thread (summed in FP32 and enlarged by 1e-4, which
+// covers the rounding; any bound above the largest eigenvalue serves).  Each warp takes one
+// row of the pattern at a time and loads four 32-entry chunks of it before searching, so that
+// several loads are in flight.  red_s: kRedDoubles doubles of shared memory.
 static __device__ double gather_submatrix(const int32_t* __restrict__ rowptr,
                                    const int32_t* __restrict__ colind,
                                    const double* __restrict__ vals, int j, int m,
@@ -148,26 +163,36 @@ static __device__ double gather_submatrix(const int32_t* __restrict__ rowptr,
   for (int k = tid; k < m; k += blockDim.x) R_s[k] = colind[base + k];
   for (int e = tid; e < m * m; e += blockDim.x) S[e] = 0.0;
   __syncthreads();
-  double wmax = 0.0;
+  float wmax = 0.f;
   const int nw = nwarps();
+  constexpr int U = 4;
   for (int k = warp; k < m; k += nw) {
     const int r = R_s[k];
     const int b = rowptr[r], e_end = rowptr[r + 1];
-    double sum = 0.0;
-    for (int e = b + lane; e < e_end; e += 32) {
-      const int l = find_sorted(R_s, m, colind[e]);
-      if (l >= 0) {
-        const double v = vals[e];
-        S[k * m + l] = v;
-        sum += fabs(v);
+    float sum = 0.f;
+    for (int e0 = b; e0 < e_end; e0 += 32 * U) {
+      int col[U];
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * 32 + lane;
+        col[u] = e < e_end ? colind[e] : -1;
+        v[u] = e < e_end ? vals[e] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int l = col[u] >= 0 ? find_sorted(R_s, m, col[u]) : -1;
+        if (l >= 0) {
+          S[k * m + l] = v[u];
+          sum += abs_f32_approx(v[u]);
+        }
       }
     }
-    sum = warp_sum(sum);
-    wmax = fmax(wmax, sum);
+    sum = warp_sum_f(sum);
     // a NaN row sum must survive the max
-    if (sum != sum) wmax = sum;
+    wmax = (sum != sum || wmax != wmax) ? sum + wmax : fmaxf(wmax, sum);
   }
-  if (lane == 0) red_s[warp] = wmax;
+  if (lane == 0) red_s[warp] = (double)wmax;
   __syncthreads();
   double lam = red_s[0];
   for (int w = 1; w < nw; ++w) {
@@ -175,7 +200,7 @@ static __device__ double gather_submatrix(const int32_t* __restrict__ rowptr,
     lam = (v != v || lam != lam) ? (v + lam) : fmax(lam, v);
   }
   __syncthreads();
-  return lam;
+  return lam * (1.0 + 1e-4);
 }
 
 // Atomic max of a non-negative double (NaN counts as +inf).

@@ -100,75 +100,109 @@ __device__ __forceinline__ void store8_slices(__half* q, size_t plane, size_t id
 }
 
 // y[i] = scale * sum_k X(i,k) x[k] for i < m, X from its first NP planes (FP32 result).
-// One warp per row, eight consecutive columns per lane with 16-byte loads; x is zero
-// beyond m up to mp.  x, y in shared memory.
-template <int NP>
+// Each warp takes RW rows at a time (their loads are in flight together), eight consecutive
+// columns per lane with 16-byte loads; x is zero beyond m up to mp.  x, y in shared memory.
+template <int NP, int RW = 4>
 __device__ void matvec_slices_f32(const __half* q, size_t plane, int ld, float scale,
                                   const float* x, float* y, int m, int mp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = warp; i < m; i += nwarps()) {
-    float acc = 0.f;
+  for (int i0 = warp * RW; i0 < m; i0 += nwarps() * RW) {
+    float acc[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) acc[r] = 0.f;
     for (int c0 = lane * 8; c0 < mp; c0 += 256) {
-      const size_t e = (size_t)i * ld + c0;
-      uint4 raw[NP];
+      uint4 raw[RW][NP];
 #pragma unroll
-      for (int k = 0; k < NP; ++k) raw[k] = *reinterpret_cast<const uint4*>(q + k * plane + e);
+      for (int r = 0; r < RW; ++r) {
+        const size_t e = (size_t)min(i0 + r, m - 1) * ld + c0;     // rows past m: discarded
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        float v = 0.f, w = 1.f;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-          v = fmaf(__half2float(reinterpret_cast<const __half*>(&raw[k])[c]), w, v);
-          w *= (1.f / 256.f);
-        }
-        acc = fmaf(v, x[c0 + c], acc);
+        for (int k = 0; k < NP; ++k) raw[r][k] = *reinterpret_cast<const uint4*>(q + k * plane + e);
       }
+      float xv[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) xv[c] = x[c0 + c];
+#pragma unroll
+      for (int r = 0; r < RW; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          float v = 0.f, w = 1.f;
+#pragma unroll
+          for (int k = 0; k < NP; ++k) {
+            v = fmaf(__half2float(reinterpret_cast<const __half*>(&raw[r][k])[c]), w, v);
+            w *= (1.f / 256.f);
+          }
+          acc[r] = fmaf(v, xv[c], acc[r]);
+        }
     }
-    acc = warp_sum_f(acc);
-    if (lane == 0) y[i] = acc * scale;
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      const float t = warp_sum_f(acc[r]);
+      if (lane == 0 && i0 + r < m) y[i0 + r] = t * scale;
+    }
   }
   __syncthreads();
 }
 
-// out[i] = sum_k A(i,k) x[k] for i < m, A from all NSL planes (scale exponent e), x given as
-// double-floats (xh, xl) zero beyond m up to mp; the result in FP64.  The planes' integers
-// recombine exactly (a = q0 2^8 + q1, b = q2 2^16 + q3 2^8 + q4, A = 2^(e-15) (a + 2^-24 b))
-// and the products a xh are accumulated error-free in double-float, so the sum keeps about
-// 44 bits.  One warp per row, eight consecutive columns per lane.
-__device__ void matvec_slices_df(const __half* q, size_t plane, int ld, int e, const float* xh,
-                                 const float* xl, double* out, int m, int mp) {
+// One pass over the sliced A (scale exponent e) for two products: out[i] = sum_k A(i,k) x[k]
+// in FP64 from x given as double-floats (xh, xl), and uo[i] = sum_k A(i,k) u[k] in FP32; all
+// vectors zero beyond m up to mp, i < m.  The planes' integers recombine exactly
+// (a = q0 2^8 + q1, b = q2 2^16 + q3 2^8 + q4, A = 2^(e-15) (a + 2^-24 b)) and the products
+// a xh are accumulated error-free in double-float, so out keeps about 44 bits.  Each warp
+// takes RW rows at a time, eight consecutive columns per lane.
+template <int RW = 2>
+__device__ void matvec2_slices(const __half* q, size_t plane, int ld, int e, const float* xh,
+                               const float* xl, double* out, const float* u, float* uo, int m,
+                               int mp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double sc = ldexp(1.0, e - 15);
-  for (int i = warp; i < m; i += nwarps()) {
-    float sh = 0.f, sl = 0.f;
-    for (int c0 = lane * 8; c0 < mp; c0 += 256) {
-      const size_t g = (size_t)i * ld + c0;
-      uint4 raw[NSL];
+  for (int i0 = warp * RW; i0 < m; i0 += nwarps() * RW) {
+    float sh[RW], sl[RW], su[RW];
 #pragma unroll
-      for (int k = 0; k < NSL; ++k) raw[k] = *reinterpret_cast<const uint4*>(q + k * plane + g);
+    for (int r = 0; r < RW; ++r) sh[r] = sl[r] = su[r] = 0.f;
+    for (int c0 = lane * 8; c0 < mp; c0 += 256) {
+      uint4 raw[RW][NSL];
+#pragma unroll
+      for (int r = 0; r < RW; ++r) {
+        const size_t g = (size_t)min(i0 + r, m - 1) * ld + c0;     // rows past m: discarded
+#pragma unroll
+        for (int k = 0; k < NSL; ++k) raw[r][k] = *reinterpret_cast<const uint4*>(q + k * plane + g);
+      }
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        float qq[NSL];
+        const float x = xh[c0 + c], xlo = xl[c0 + c], uv = u[c0 + c];
 #pragma unroll
-        for (int k = 0; k < NSL; ++k) qq[k] = __half2float(reinterpret_cast<const __half*>(&raw[k])[c]);
-        const float a = __fmaf_rn(qq[0], 256.f, qq[1]);
-        const float b = __fmaf_rn(qq[2], 65536.f, __fmaf_rn(qq[3], 256.f, qq[4]));
-        const float x = xh[c0 + c];
-        const float pr = __fmul_rn(a, x);
-        const float pe = __fmaf_rn(a, x, -pr);          // a x - pr exactly
-        float t;
-        two_sum(sh, pr, sh, t);
-        sl = __fadd_rn(sl, __fadd_rn(t, __fmaf_rn(a, xl[c0 + c], __fmaf_rn(b * (1.f / 16777216.f), x, pe))));
+        for (int r = 0; r < RW; ++r) {
+          float qq[NSL];
+#pragma unroll
+          for (int k = 0; k < NSL; ++k)
+            qq[k] = __half2float(reinterpret_cast<const __half*>(&raw[r][k])[c]);
+          const float a = __fmaf_rn(qq[0], 256.f, qq[1]);
+          const float b = __fmaf_rn(qq[2], 65536.f, __fmaf_rn(qq[3], 256.f, qq[4]));
+          const float pr = __fmul_rn(a, x);
+          const float pe = __fmaf_rn(a, x, -pr);          // a x - pr exactly
+          float t;
+          two_sum(sh[r], pr, sh[r], t);
+          sl[r] = __fadd_rn(sl[r], __fadd_rn(t, __fmaf_rn(a, xlo, __fmaf_rn(b * (1.f / 16777216.f), x, pe))));
+          su[r] = __fmaf_rn(__fmaf_rn(qq[2], 1.f / 256.f, a), uv, su[r]);   // FP32, 3 planes
+        }
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
-      const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
-      float t;
-      two_sum(sh, oh, sh, t);
-      sl = __fadd_rn(sl, __fadd_rn(ol, t));
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      float h = sh[r], l = sl[r], uu = su[r];
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+        uu += __shfl_xor_sync(0xffffffffu, uu, o);
+        float t;
+        two_sum(h, oh, h, t);
+        l = __fadd_rn(l, __fadd_rn(ol, t));
+      }
+      if (lane == 0 && i0 + r < m) {
+        out[i0 + r] = ((double)h + (double)l) * sc;
+        uo[i0 + r] = uu * (float)sc;
+      }
     }
-    if (lane == 0) out[i] = ((double)sh + (double)sl) * sc;
   }
   __syncthreads();
 }
@@ -773,11 +807,12 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
         t_s[i] = 0.f;
       }
       __syncthreads();
-      matvec_slices_df(Mk.q, plane, LD, Mk.e, yh_s, yl_s, my_s, m, mp);
+      // M y (FP64) and M u (FP32) in one pass, then the other p - 1 products for u
+      matvec2_slices(Mk.q, plane, LD, Mk.e, yh_s, yl_s, my_s, u_s, t_s, m, mp);
       for (int i = tid; i < m; i += blockDim.x) yg[i] = c * (alpha * y_s[i] - my_s[i]);
       const float cf = (float)c, af = (float)alpha;
       for (int t = 0; t < p; ++t) {
-        matvec_slices_f32<3>(Mk.q, plane, LD, ldexpf(1.f, Mk.e - 7), u_s, t_s, m, mp);
+        if (t > 0) matvec_slices_f32<3>(Mk.q, plane, LD, ldexpf(1.f, Mk.e - 7), u_s, t_s, m, mp);
         for (int i = tid; i < m; i += blockDim.x) u_s[i] = cf * (af * u_s[i] - t_s[i]);
         __syncthreads();
       }
