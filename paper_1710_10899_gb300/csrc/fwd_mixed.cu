@@ -371,17 +371,22 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
             break;
           }
           tc::tc_fence_after();
+          // operand descriptors of the stage; every plane / k-step offset below is a
+          // compile-time constant added to the 14-bit start-address field (no carry: shared
+          // addresses stay below 2^18 bytes)
           const uint32_t sa = tc::saddr(c.stages + s * TC_STAGE_BYTES);
-          const uint32_t sb = sa + NSL * TC_A_PLANE;
+          const uint64_t da0 = tc::desc_sw64(sa);
+          const uint64_t db0 = tc::desc_sw64(sa + NSL * TC_A_PLANE);
+          const uint32_t acc0 = kt != 0;               // the first k-step overwrites
 #pragma unroll
           for (int kk = 0; kk < TC_K / 16; ++kk) {
 #pragma unroll
             for (int L = 0; L < NSL; ++L) {
 #pragma unroll
               for (int sa_i = 0; sa_i <= L; ++sa_i) {
-                const uint64_t da = tc::desc_sw64(sa + sa_i * TC_A_PLANE + kk * 32);
-                const uint64_t db = tc::desc_sw64(sb + (L - sa_i) * TC_B_PLANE + kk * 32);
-                tc::mma_f16(d0 + L * TC_N, da, db, idesc, (kt | kk | sa_i) != 0 ? 1u : 0u);
+                const uint64_t da = da0 + (uint64_t)((sa_i * TC_A_PLANE + kk * 32) >> 4);
+                const uint64_t db = db0 + (uint64_t)(((L - sa_i) * TC_B_PLANE + kk * 32) >> 4);
+                tc::mma_f16(d0 + L * TC_N, da, db, idesc, (kk | sa_i) != 0 ? 1u : acc0);
               }
             }
           }
@@ -398,7 +403,10 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
     }
   } else {                                             // ---- epilogue (TMEM lanes 0..127)
     const int q4 = warp & 3, half = warp >> 2;
-    const float cscale = ldexpf(1.f, A.e + B.e - 14);
+    // the level sums count in units of cscale = 2^(A.e + B.e - 14), Y's planes in units of
+    // 2^(Y.e - 15)
+    const float alpha_s = ldexpf(io.alpha, Y.e - 15 - (A.e + B.e - 14));
+    const float c_s = ldexpf(io.c, A.e + B.e - 14);
     float nrm = 0.f, amax = 0.f;
     for (int t = 0; t < ntiles; ++t) {
       const uint32_t b = st.ept & 1;
@@ -420,14 +428,35 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
         if (row < mp) {
           const int j0 = tn * TC_N + c0;
           const size_t idx0 = (size_t)row * io.ld + j0;
-          float yh[8], yl[8], oh[8], ol[8];
-          load8_df(Y.q, io.plane, idx0, Y.e, yh, yl);
+          float oh[8], ol[8];
+          uint4 yr[NSL];
+#pragma unroll
+          for (int k = 0; k < NSL; ++k)
+            yr[k] = *reinterpret_cast<const uint4*>(Y.q + k * io.plane + idx0);
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
-            const float lv[NSL] = {acc[0][k], acc[1][k], acc[2][k], acc[3][k], acc[4][k]};
-            float vh, vl;
-            combine_levels(lv, cscale, vh, vl);
-            aff_df(vh, vl, yh[k], yl[k], io.alpha, io.c, oh[k], ol[k]);
+            float yq[NSL];
+#pragma unroll
+            for (int s2 = 0; s2 < NSL; ++s2)
+              yq[s2] = __half2float(reinterpret_cast<const __half*>(&yr[s2])[k]);
+            // y / 2^(Y.e-15) = ya + yb, exact (ya an integer below 2^16, yb below 1)
+            const float ya = __fmaf_rn(yq[0], 256.f, yq[1]);
+            const float yb = __fmaf_rn(yq[2], 1.f / 256.f, __fmaf_rn(yq[3], 1.f / 65536.f,
+                                                                     yq[4] * (1.f / 16777216.f)));
+            // w = v / cscale = acc0 + 2^-8 acc1 + (levels 2..4), the first two exactly
+            float wh, wl;
+            two_sum(acc[0][k], acc[1][k] * (1.f / 256.f), wh, wl);
+            wl = __fadd_rn(wl, __fmaf_rn(acc[4][k], 1.f / 4294967296.f,
+                                         __fmaf_rn(acc[3][k], 1.f / 16777216.f,
+                                                   acc[2][k] * (1.f / 65536.f))));
+            // out = c cscale (alpha' y - w), alpha' = alpha 2^(Y.e-15) / cscale (exact)
+            const float p1 = __fmul_rn(alpha_s, ya);
+            const float e1 = __fmaf_rn(alpha_s, yb, __fmaf_rn(alpha_s, ya, -p1));
+            float d, de;
+            two_sum(p1, -wh, d, de);
+            de = __fadd_rn(de, __fsub_rn(e1, wl));
+            oh[k] = __fmul_rn(c_s, d);
+            ol[k] = __fmaf_rn(c_s, de, __fmaf_rn(c_s, d, -oh[k]));
           }
           store8_slices(C.q, io.plane, idx0, oh, ol, C.e);
           if (flags & EPI_AMAX) {
