@@ -23,7 +23,7 @@
 // The products of these integers are exact, and every level-0 partial sum is an integer
 // below 2^14 K, so for K <= 1024 the tensor cores accumulate level 0 exactly (level 1
 // below 2^15 K: exact for K <= 512, and its weight is 2^-8 anyway); levels 2..4 carry
-// weights 2^-16..2^-32.  The levels dropped (s + t >= 5) bound the normwise error of a
+// weights 2^-16..2^-32.  Orders above 1024 raise every exponent by one (|q0| <= 64).  The levels dropped (s + t >= 5) bound the normwise error of a
 // product near 2^-39 sqrt(K) of max|A| max|B|.  The epilogue combines the levels in
 // double-float (FP32 pairs) and re-splits the result.  (With four planes, the ~2^-31
 // per-product error, kept by every iteration, left ~6e-7 in the result; measured.)
@@ -82,6 +82,10 @@ struct GemmIO {     // what every GEMM call shares within one submatrix
 
 // Exponent for values bounded by b (with a relative margin for rounding).
 __device__ __forceinline__ int exp_of(float b) { return exp_bound(b * (1.f + 1e-6f)); }
+
+// Extra exponent for orders above 1024: with |q0| <= 64 every level-0 partial sum stays an
+// integer below 2^12 K < 2^24 up to K = 4096 (one of the 39 bits is given up).
+__device__ __forceinline__ int exp_bias(int mp) { return mp > 1024 ? 1 : 0; }
 
 // Slices of 8 consecutive values -> one 16-byte store per plane.
 __device__ __forceinline__ void store8_slices(__half* q, size_t plane, size_t idx0,
@@ -238,7 +242,7 @@ __device__ float power_max_slices(const __half* q, size_t plane, int ld, float s
 // with M_0 from its two leading planes, from a fixed +-1 vector.  ||(I - M_0) v|| for a unit
 // v never exceeds 1 - lambda_min(M_0), so the estimate errs towards a larger lower end (the
 // raw estimate; the steps are steered with half of it).  a_s, b_s: mp floats; zero beyond m.
-__device__ float start_lo_slices(const __half* q, size_t plane, int ld, int m, int mp,
+__device__ float start_lo_slices(const __half* q, size_t plane, int ld, int e, int m, int mp,
                                  float* a_s, float* b_s, float* red_s) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float inv_n = rsqrtf((float)m);
@@ -249,7 +253,7 @@ __device__ float start_lo_slices(const __half* q, size_t plane, int ld, int m, i
   __syncthreads();
   float nb = 1.f;
   for (int t = 0; t < kStartLoSteps; ++t) {
-    matvec_slices_f32<2>(q, plane, ld, ldexpf(1.f, E_M - 7), a_s, b_s, m, mp);   // b = M_0 a
+    matvec_slices_f32<2>(q, plane, ld, ldexpf(1.f, e - 7), a_s, b_s, m, mp);   // b = M_0 a
     float part = 0.f;
     for (int i = tid; i < m; i += blockDim.x) {
       const float d = a_s[i] - b_s[i];
@@ -751,9 +755,11 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     // Two X buffers (p = 1 only) and three buffers for M_k and the partial products T^s M_k
     // (M_k is the A operand of all p products of an iteration and stays in place).
     Mat X[2] = {{hb + 0 * NSL * plane, 0, plane_base + 0}, {hb + 1 * NSL * plane, 0, plane_base + 5}};
-    Mat B3[3] = {{hb + 2 * NSL * plane, E_M, plane_base + 10},
-                 {hb + 3 * NSL * plane, E_M, plane_base + 15},
-                 {hb + 4 * NSL * plane, E_M, plane_base + 20}};
+    const int eb = exp_bias(mp);
+    const int e_m = E_M + eb;
+    Mat B3[3] = {{hb + 2 * NSL * plane, e_m, plane_base + 10},
+                 {hb + 3 * NSL * plane, e_m, plane_base + 15},
+                 {hb + 4 * NSL * plane, e_m, plane_base + 20}};
     double* yg = reinterpret_cast<double*>(hb + 34 * plane);     // tracked X_k e_pos (FP64)
     float* ug = reinterpret_cast<float*>(yg + SUBMAT_MAX_M);     // tracked residual vector
 
@@ -784,7 +790,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
             nrm += ev * ev;
           }
         }
-        store8_slices(B3[0].q, plane, (size_t)i * LD + j0, mh, ml, E_M);
+        store8_slices(B3[0].q, plane, (size_t)i * LD + j0, mh, ml, e_m);
       }
       nrm = warp_sum_f(nrm);
       if ((tid & 31) == 0) atomicAdd(norm2_s, nrm);
@@ -794,7 +800,8 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
 
     // lower end of M_0's spectrum: the raw estimate gives the condition estimate
     // lambda_bar / lambda_min(S) = 1 / lambda_min(M_0), half of it steers the steps
-    const float lo_raw = start_lo_slices(B3[0].q, plane, LD, m, mp, reinterpret_cast<float*>(v_s),
+    const float lo_raw = start_lo_slices(B3[0].q, plane, LD, e_m, m, mp,
+                                         reinterpret_cast<float*>(v_s),
                                          reinterpret_cast<float*>(w_s),
                                          reinterpret_cast<float*>(red_s));
     float lo = 0.5f * lo_raw;
@@ -870,7 +877,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
         vec_step(Mk, (double)st.c, (double)st.alpha);
       } else if (iters == 0) {
         // X_1 = T_0 (elementwise from M_0)
-        X[0].e = exp_of(st.tmax);
+        X[0].e = exp_of(st.tmax) + eb;
         xmax = st.tmax;
         for (int e = tid; e < mp * mp8; e += blockDim.x) {
           const int i = e / mp8, j0 = (e % mp8) * 8;
@@ -891,7 +898,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
       } else {
         // X_{k+1} = c (alpha X_k - X_k M_k); X_k, T_k SPD and commuting with T_k <= tmax I,
         // so the largest entry (a diagonal one) grows at most by tmax
-        X[xc ^ 1].e = exp_of(xmax * st.tmax);
+        X[xc ^ 1].e = exp_of(xmax * st.tmax) + eb;
         if (tid == 0) *amax_s = 0u;
         __syncthreads();
         if (!gemm(X[xc], Mk, X[xc ^ 1], X[xc], EPI_AMAX)) { stop = true; break; }
@@ -903,7 +910,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
       int src = mi, dst = (mi + 1) % 3;
       for (int s = 1; s <= p; ++s) {
         const bool last = (s == p);
-        B3[dst].e = last ? E_M : exp_of(partial_bound(st, s));
+        B3[dst].e = last ? e_m : exp_of(partial_bound(st, s)) + eb;
         if (last) {
           if (tid == 0) *norm2_s = 0.f;
           __syncthreads();
@@ -950,7 +957,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     } else if (!bad) {
       io.c = 1.f;                                // p = 1: X (2 I - M)
       io.alpha = 2.f;
-      X[xc ^ 1].e = exp_of(xmax * 2.f);
+      X[xc ^ 1].e = exp_of(xmax * 2.f) + eb;
       if (tid == 0) *amax_s = 0u;
       __syncthreads();
       if (!gemm(X[xc], B3[mi], X[xc ^ 1], X[xc], EPI_AMAX)) break;

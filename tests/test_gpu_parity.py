@@ -134,6 +134,27 @@ def test_dense_pattern_equals_full_root(sm):
     assert np.abs(yd - full.T).max() / np.abs(full).max() < 1e-6
 
 
+@pytest.mark.parametrize("p", [1, 2])
+def test_order_above_1024(sm, p):
+    # arrow + band: row 0's submatrix is the whole 1200 x 1200 matrix (padded order 1216),
+    # where the mixed path's slices give up one bit to keep level-0 sums exact
+    n = 1200
+    rng = np.random.default_rng(7)
+    dense = np.eye(n) * 2.0
+    for k in (1, 2):
+        off = 0.15 * rng.uniform(0.5, 1.0, n - k)
+        dense += np.diag(off, k) + np.diag(off, -k)
+    arrow = 0.02 * rng.uniform(0.5, 1.0, n - 1)
+    dense[0, 1:] = arrow
+    dense[1:, 0] = arrow
+    a = wl.dense_to_csr(dense)
+    plan, y = run(sm, a, p, "mixed")
+    rows = [0, 1, 2, 600, n - 1]
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, p, rows=rows)
+    assert row_errors(a, y, ref, rows).max() <= TOL["mixed"]
+    assert plan.report()["n_fallback"] == 0
+
+
 def test_forced_fallback_matches_oracle(sm):
     a = wl.overlap_uniform(n=1500)
     plan, y = run(sm, a, 2, "mixed", resid_tol=1e-300)
