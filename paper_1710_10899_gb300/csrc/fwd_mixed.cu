@@ -315,6 +315,68 @@ struct TcCtx {
   const CUtensorMap* tm_b;
 };
 
+// Output tiles of a symmetric product: row block tm (128 rows) needs only the column tiles
+// that reach its diagonal block, tn >= skip(tm) = floor(128 tm / 48); the tiles left of them
+// lie wholly below the diagonal and are written as mirror images by the tiles above
+// (mirror_needed).  All three roles enumerate the tiles in the same order.
+__device__ __forceinline__ int tc_skip(int tm) { return (TC_M * tm) / TC_N; }
+__device__ __forceinline__ int tc_ntiles(int ntm, int ntn) {
+  int n = 0;
+  for (int tm = 0; tm < ntm; ++tm) n += max(0, ntn - tc_skip(tm));
+  return n;
+}
+__device__ __forceinline__ void tc_tile(int t, int ntn, int& tm, int& tn) {
+  tm = 0;
+  for (;;) {
+    const int cnt = max(0, ntn - tc_skip(tm));
+    if (t < cnt) break;
+    t -= cnt;
+    ++tm;
+  }
+  tn = tc_skip(tm) + t;
+}
+// Entry (i, j) computed in row block tm is also stored at (j, i) when (j, i) lies in a
+// skipped tile: j's row block is below tm and i's column tile there is skipped.
+__device__ __forceinline__ bool mirror_needed(int i, int j, int tm) {
+  const int tmj = j / TC_M;
+  return tmj > tm && (i / TC_N) < tc_skip(tmj);
+}
+
+// Planes of the eight entries (row, j0..j0+7) of a symmetric product: one 16-byte store per
+// plane, and each entry whose mirror lies in a skipped tile also at (j, row) (a warp's 32
+// consecutive rows make these 64-byte contiguous stores).  Returns the mask of mirrored
+// entries.
+__device__ __forceinline__ unsigned store8_sym(__half* q, size_t plane, int ld, int row,
+                                               int j0, int tm, const float* vh, const float* vl,
+                                               int e) {
+  __align__(16) __half out[NSL][8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float s[NSL];
+    make_slices(vh[c], vl[c], e, s);
+#pragma unroll
+    for (int k = 0; k < NSL; ++k) out[k][c] = __float2half_rn(s[k]);
+  }
+  const size_t idx0 = (size_t)row * ld + j0;
+#pragma unroll
+  for (int k = 0; k < NSL; ++k)
+    *reinterpret_cast<uint4*>(q + k * plane + idx0) = *reinterpret_cast<const uint4*>(out[k]);
+  unsigned mask = 0u;
+  if (mirror_needed(row, j0 + 7, tm)) {             // the chunk reaches a later row block
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = j0 + c;
+      if (mirror_needed(row, j, tm)) {
+        mask |= 1u << c;
+        const size_t m_idx = (size_t)j * ld + row;
+#pragma unroll
+        for (int k = 0; k < NSL; ++k) q[k * plane + m_idx] = out[k][c];
+      }
+    }
+  }
+  return mask;
+}
+
 // C = A B^T on the tcgen05 engine (see the header comment).  All TC_THREADS threads call it.
 // Returns false if a pipeline wait timed out (the CTA then stops).
 __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y, int flags,
@@ -322,7 +384,7 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mp = io.mp;
   const int ntm = (mp + TC_M - 1) / TC_M, ntn = (mp + TC_N - 1) / TC_N, KT = mp / TC_K;
-  const int ntiles = ntm * ntn;
+  const int ntiles = tc_ntiles(ntm, ntn);
   // generic-proxy writes (planes, shared vectors) before async-proxy reads/writes
   tc::fence_proxy_async_global();
   tc::fence_proxy_async_shared();
@@ -331,7 +393,8 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
   if (warp == TC_TMA_WARP) {
     if (lane == 0) {                                   // ---- TMA producer
       for (int t = 0; t < ntiles && !*c.abort_s; ++t) {
-        const int tm = t / ntn, tn = t % ntn;
+        int tm, tn;
+        tc_tile(t, ntn, tm, tn);
         for (int kt = 0; kt < KT; ++kt) {
           const uint32_t s = st.pit % TC_STAGES, round = st.pit / TC_STAGES;
           if (round > 0 && !tc::mbar_wait(&c.empty[s], (round - 1) & 1, TC_WAIT_LIMIT)) {
@@ -356,7 +419,8 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
   } else if (warp == TC_MMA_WARP) {
     if (lane == 0) {                                   // ---- MMA issuer
       for (int t = 0; t < ntiles && !*c.abort_s; ++t) {
-        const int tn = t % ntn;
+        int tm, tn;
+        tc_tile(t, ntn, tm, tn);
         const int nw = min(TC_N, mp - tn * TC_N);      // 48, or 16 / 32 for the last tile
         const uint32_t idesc = tc::idesc_f16(TC_M, nw);
         const uint32_t b = st.tmt & 1;
@@ -419,7 +483,8 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
         break;
       }
       tc::tc_fence_after();
-      const int tm = t / ntn, tn = t % ntn;
+      int tm, tn;
+      tc_tile(t, ntn, tm, tn);
       const int nw = min(TC_N, mp - tn * TC_N);
       const int row = tm * TC_M + q4 * 32 + lane;
       const uint32_t tbase = c.tmem + ((uint32_t)(q4 * 32) << 16) + b * TC_BUF_COLS;
@@ -462,7 +527,7 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
             oh[k] = __fmul_rn(c_s, d);
             ol[k] = __fmaf_rn(c_s, de, __fmaf_rn(c_s, d, -oh[k]));
           }
-          store8_slices(C.q, io.plane, idx0, oh, ol, C.e);
+          const unsigned mir = store8_sym(C.q, io.plane, io.ld, row, j0, tm, oh, ol, C.e);
           if (flags & EPI_AMAX) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) amax = fmaxf(amax, fabsf(oh[k]));
@@ -474,7 +539,7 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
               const bool in = (row < io.m) && (jj < io.m);
               const float d = (row == jj) ? 1.f : 0.f;
               const float ev = in ? __fadd_rn(__fsub_rn(oh[k], d), ol[k]) : 0.f;
-              nrm += ev * ev;
+              nrm += ((mir >> k) & 1u) ? 2.f * ev * ev : ev * ev;   // a mirrored entry counts twice
             }
           }
         }
