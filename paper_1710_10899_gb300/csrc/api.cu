@@ -13,6 +13,7 @@
 
 namespace submat {
 cudaError_t set_attr_mixed();
+int mixed_ctas_per_sm();           // CTAs per SM of the tcgen05 engine
 cudaError_t set_attr_fp64();
 cudaError_t set_attr_eig();
 }  // namespace submat
@@ -314,7 +315,8 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   size_t stride = mixed ? scratch_mixed(P->ld) : std::max(scratch_eig(mp), scratch_fp64(mp));
   stride = (stride + 1023) / 1024 * 1024;
   P->stride = stride;
-  P->grid = std::max(1, std::min(P->n_sm, n));
+  const int ctas = (o.precision == SUBMAT_PREC_MIXED_F16) ? mixed_ctas_per_sm() : 1;
+  P->grid = std::max(1, std::min(P->n_sm * ctas, n));
   PLAN_TRY(cudaMalloc(&P->d_scratch, stride * (size_t)P->grid));
   if (mixed && o.precision == SUBMAT_PREC_MIXED_F16) {
     // TMA descriptors over all CTAs' planes: dims (LD cols, LD rows, planes), 64-byte swizzle

@@ -151,24 +151,29 @@ __device__ __forceinline__ float abs_f32_approx(double v) {
 // Algorithm 1 for row j (value part): S[k*m + l] = A[R[k]][R[l]] in FP64 (zero where not
 // stored), R staged in shared memory (R_s, m ints), and the Gershgorin bound
 // max_k sum_l |S_kl| returned to every thread (summed in FP32 and enlarged by 1e-4, which
-// covers the rounding; any bound above the largest eigenvalue serves).  Each warp takes one
-// row of the pattern at a time and loads four 32-entry chunks of it before searching, so that
-// several loads are in flight.  red_s: kRedDoubles doubles of shared memory.
+// covers the rounding; any bound above the largest eigenvalue serves).  The extents of all
+// m pattern rows are loaded first, in parallel; then each warp takes one row at a time and
+// loads up to eight 32-entry chunks of it before searching, so that a row costs one round
+// trip to memory.  red_s: kRedDoubles doubles of shared memory.
 static __device__ double gather_submatrix(const int32_t* __restrict__ rowptr,
                                    const int32_t* __restrict__ colind,
                                    const double* __restrict__ vals, int j, int m,
                                    int32_t* R_s, double* __restrict__ S, double* red_s) {
+  __shared__ int2 ext_s[SUBMAT_MAX_M];               // [rowptr[R_k], rowptr[R_k + 1])
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int base = rowptr[j];
-  for (int k = tid; k < m; k += blockDim.x) R_s[k] = colind[base + k];
+  for (int k = tid; k < m; k += blockDim.x) {
+    const int r = colind[base + k];
+    R_s[k] = r;
+    ext_s[k] = make_int2(rowptr[r], rowptr[r + 1]);
+  }
   for (int e = tid; e < m * m; e += blockDim.x) S[e] = 0.0;
   __syncthreads();
   float wmax = 0.f;
   const int nw = nwarps();
-  constexpr int U = 4;
+  constexpr int U = 8;
   for (int k = warp; k < m; k += nw) {
-    const int r = R_s[k];
-    const int b = rowptr[r], e_end = rowptr[r + 1];
+    const int b = ext_s[k].x, e_end = ext_s[k].y;
     float sum = 0.f;
     for (int e0 = b; e0 < e_end; e0 += 32 * U) {
       int col[U];

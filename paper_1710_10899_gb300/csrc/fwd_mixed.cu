@@ -282,19 +282,25 @@ __device__ float start_lo_slices(const __half* q, size_t plane, int ld, int e, i
 // 32 wide).  Five level accumulators of 48 columns make one 240-column TMEM buffer; two
 // buffers (480 of 512 columns) let the MMAs of tile t+1 run while the epilogue drains t.
 constexpr int TC_M = 128, TC_N = 48, TC_K = 32;        // tile and k-slice
-constexpr int TC_STAGES = 3;
+// CTAs per SM: two CTAs, each with half of TMEM and shared memory, let one CTA's
+// latency-bound phases (gather, vector steps) and epilogues overlap the other's MMAs.
+constexpr int TC_CTAS = 1;
+constexpr int TC_NBUF = TC_CTAS == 1 ? 2 : 1;          // TMEM accumulator buffers
+constexpr int TC_STAGES = TC_CTAS == 1 ? 3 : 2;
 constexpr int TC_A_PLANE = TC_M * TC_K * 2;            // 8192 B
 constexpr int TC_B_PLANE = TC_N * TC_K * 2;            // 3072 B
 constexpr int TC_STAGE_BYTES = NSL * (TC_A_PLANE + TC_B_PLANE);   // 56320 B
 constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 168960 B
 constexpr int TC_BUF_COLS = NSL * TC_N;                // 240 TMEM columns per buffer
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;           // polls before a wait gives up
-constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr uint32_t TC_TMEM_COLS = TC_CTAS == 1 ? 512 : 256;
+static_assert(TC_NBUF * TC_BUF_COLS <= (int)TC_TMEM_COLS, "TMEM budget");
 // tcgen05 CTA: warps 0-7 run the epilogue (warp w: TMEM lane quarter w % 4, column half
 // w / 4 of the tile), warp 8 issues TMA, warp 9 issues MMAs.
-constexpr int TC_EPI_WARPS = 8;
-constexpr int TC_THREADS = 320;
-constexpr int TC_TMA_WARP = 8, TC_MMA_WARP = 9;
+constexpr int TC_EPI_WARPS = TC_CTAS == 1 ? 8 : 4;
+constexpr int TC_THREADS = (TC_EPI_WARPS + 2) * 32;
+constexpr int TC_TMA_WARP = TC_EPI_WARPS, TC_MMA_WARP = TC_EPI_WARPS + 1;
+constexpr int TC_EPI_COLS = TC_N * 4 / TC_EPI_WARPS;  // tile columns per epilogue warp
 
 struct TcState {            // pipeline counters; each role keeps its own copy
   uint32_t pit = 0;         // stages issued (TMA)
@@ -423,9 +429,9 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
         tc_tile(t, ntn, tm, tn);
         const int nw = min(TC_N, mp - tn * TC_N);      // 48, or 16 / 32 for the last tile
         const uint32_t idesc = tc::idesc_f16(TC_M, nw);
-        const uint32_t b = st.tmt & 1;
-        if (st.tmt >= 2 &&
-            !tc::mbar_wait(&c.tmem_empty[b], ((st.tmt >> 1) - 1) & 1, TC_WAIT_LIMIT)) {
+        const uint32_t b = st.tmt % TC_NBUF;
+        if (st.tmt >= TC_NBUF &&
+            !tc::mbar_wait(&c.tmem_empty[b], ((st.tmt / TC_NBUF) - 1) & 1, TC_WAIT_LIMIT)) {
           *c.abort_s = 1;
           break;
         }
@@ -477,8 +483,8 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
     const float c_s = ldexpf(io.c, A.e + B.e - 14);
     float nrm = 0.f, amax = 0.f;
     for (int t = 0; t < ntiles; ++t) {
-      const uint32_t b = st.ept & 1;
-      if (!tc::mbar_wait(&c.tmem_full[b], (st.ept >> 1) & 1, TC_WAIT_LIMIT)) {
+      const uint32_t b = st.ept % TC_NBUF;
+      if (!tc::mbar_wait(&c.tmem_full[b], (st.ept / TC_NBUF) & 1, TC_WAIT_LIMIT)) {
         *c.abort_s = 1;
         break;
       }
@@ -488,7 +494,7 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
       const int nw = min(TC_N, mp - tn * TC_N);
       const int row = tm * TC_M + q4 * 32 + lane;
       const uint32_t tbase = c.tmem + ((uint32_t)(q4 * 32) << 16) + b * TC_BUF_COLS;
-      for (int c0 = half * (TC_N / 2); c0 < (half + 1) * (TC_N / 2); c0 += 8) {
+      for (int c0 = half * TC_EPI_COLS; c0 < (half + 1) * TC_EPI_COLS; c0 += 8) {
         if (c0 >= nw) break;                           // warp-uniform
         float acc[NSL][8];
 #pragma unroll
@@ -751,7 +757,7 @@ constexpr size_t kVecBytes = 4 * SUBMAT_MAX_M * sizeof(double) + kRedDoubles * s
 static_assert(kVecBytes <= (size_t)SY_STAGE_AREA, "vector area must fit in the stage area");
 
 template <bool TC>
-__global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
+__global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
     fwd_mixed_kernel(const __grid_constant__ FwdArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
@@ -762,7 +768,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
   double* red_s = w_s + SUBMAT_MAX_M;                 // kRedDoubles doubles
   int32_t* R_s = reinterpret_cast<int32_t*>(red_s + kRedDoubles);
   unsigned char* tail = sm + stage_area<TC>();
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tail);  // full[3] empty[3] tmem_full[2] tmem_empty[2]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tail);  // full, empty [TC_STAGES], tmem_full, tmem_empty [TC_NBUF]
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tail + 96);
   int* abort_s = reinterpret_cast<int*>(tail + 100);
   float* norm2_s = reinterpret_cast<float*>(tail + 104);
@@ -781,9 +787,9 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
   TcState tst;
   if (TC) {
     if (tid == 0) {
-      for (int i = 0; i < 2 * TC_STAGES + 2; ++i) tc::mbar_init(&bars[i], 1);
-      tc::mbar_init(&bars[2 * TC_STAGES + 2], TC_EPI_WARPS * 32);
-      tc::mbar_init(&bars[2 * TC_STAGES + 3], TC_EPI_WARPS * 32);
+      for (int i = 0; i < 2 * TC_STAGES + TC_NBUF; ++i) tc::mbar_init(&bars[i], 1);
+      for (int i = 0; i < TC_NBUF; ++i)
+        tc::mbar_init(&bars[2 * TC_STAGES + TC_NBUF + i], TC_EPI_WARPS * 32);
       *abort_s = 0;
       tc::fence_mbar_init();
     }
@@ -795,7 +801,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     tcx.full = bars;
     tcx.empty = bars + TC_STAGES;
     tcx.tmem_full = bars + 2 * TC_STAGES;
-    tcx.tmem_empty = bars + 2 * TC_STAGES + 2;
+    tcx.tmem_empty = bars + 2 * TC_STAGES + TC_NBUF;
     tcx.abort_s = abort_s;
     tcx.tmem = *tmem_holder;
     tcx.tm_a = &a.tm_a;
@@ -1085,11 +1091,18 @@ cudaError_t launch_fwd_mixed(const FwdArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+int mixed_ctas_per_sm() { return TC_CTAS; }
+
 cudaError_t set_attr_mixed() {
   cudaError_t e = cudaFuncSetAttribute(fwd_mixed_kernel<true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes<true>());
   if (e != cudaSuccess) return e;
+  if (TC_CTAS > 1) {                                   // room for two CTAs' shared memory
+    e = cudaFuncSetAttribute(fwd_mixed_kernel<true>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(fwd_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_bytes<false>());
 }
