@@ -103,14 +103,34 @@ __device__ __forceinline__ void store8_slices(__half* q, size_t plane, size_t id
     *reinterpret_cast<uint4*>(q + k * plane + idx0) = *reinterpret_cast<const uint4*>(out[k]);
 }
 
+// Barrier of a warp group: BAR = 0 is the whole block (__syncthreads); BAR = kEpiBar is the
+// tcgen05 engine's epilogue warps 0..kEpiGroupWarps-1 (a named barrier), which run vector
+// work while the MMA and TMA warps run a GEMM.
+// CTAs per SM of the tcgen05 engine: two CTAs, each with half of TMEM and shared memory,
+// would let one CTA's latency-bound phases overlap the other's MMAs (measured slower).
+constexpr int TC_CTAS = 1;
+constexpr int kEpiBar = 3;
+constexpr int kEpiGroupWarps = TC_CTAS == 1 ? 8 : 4;
+template <int BAR>
+__device__ __forceinline__ void grp_sync() {
+  if (BAR == 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, %1;\n" ::"n"(BAR), "n"(kEpiGroupWarps * 32) : "memory");
+}
+template <int BAR>
+__device__ __forceinline__ int grp_warps() { return BAR == 0 ? nwarps() : kEpiGroupWarps; }
+template <int BAR>
+__device__ __forceinline__ int grp_threads() { return BAR == 0 ? (int)blockDim.x : kEpiGroupWarps * 32; }
+
 // y[i] = scale * sum_k X(i,k) x[k] for i < m, X from its first NP planes (FP32 result).
 // Each warp takes RW rows at a time (their loads are in flight together), eight consecutive
 // columns per lane with 16-byte loads; x is zero beyond m up to mp.  x, y in shared memory.
-template <int NP, int RW = 4>
+template <int NP, int RW = 4, int BAR = 0>
 __device__ void matvec_slices_f32(const __half* q, size_t plane, int ld, float scale,
                                   const float* x, float* y, int m, int mp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i0 = warp * RW; i0 < m; i0 += nwarps() * RW) {
+  for (int i0 = warp * RW; i0 < m; i0 += grp_warps<BAR>() * RW) {
     float acc[RW];
 #pragma unroll
     for (int r = 0; r < RW; ++r) acc[r] = 0.f;
@@ -144,7 +164,7 @@ __device__ void matvec_slices_f32(const __half* q, size_t plane, int ld, float s
       if (lane == 0 && i0 + r < m) y[i0 + r] = t * scale;
     }
   }
-  __syncthreads();
+  grp_sync<BAR>();
 }
 
 // One pass over the sliced A (scale exponent e) for two products: out[i] = sum_k A(i,k) x[k]
@@ -153,13 +173,13 @@ __device__ void matvec_slices_f32(const __half* q, size_t plane, int ld, float s
 // (a = q0 2^8 + q1, b = q2 2^16 + q3 2^8 + q4, A = 2^(e-15) (a + 2^-24 b)) and the products
 // a xh are accumulated error-free in double-float, so out keeps about 44 bits.  Each warp
 // takes RW rows at a time, eight consecutive columns per lane.
-template <int RW = 2>
+template <int RW = 2, int BAR = 0>
 __device__ void matvec2_slices(const __half* q, size_t plane, int ld, int e, const float* xh,
                                const float* xl, double* out, const float* u, float* uo, int m,
                                int mp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double sc = ldexp(1.0, e - 15);
-  for (int i0 = warp * RW; i0 < m; i0 += nwarps() * RW) {
+  for (int i0 = warp * RW; i0 < m; i0 += grp_warps<BAR>() * RW) {
     float sh[RW], sl[RW], su[RW];
 #pragma unroll
     for (int r = 0; r < RW; ++r) sh[r] = sl[r] = su[r] = 0.f;
@@ -208,7 +228,47 @@ __device__ void matvec2_slices(const __half* q, size_t plane, int ld, int e, con
       }
     }
   }
-  __syncthreads();
+  grp_sync<BAR>();
+}
+
+// The step T = c (alpha I - M_k) applied to the vectors carried for p >= 2: y <- T y (FP64
+// result of a double-float product), u <- T^p u (FP32).  All vectors live in the CTA's
+// global scratch and are zero beyond m up to mp.  Run by a warp group (BAR, see grp_sync):
+// inside the tcgen05 engine the epilogue warps do it while the MMA warp starts the
+// iteration's first GEMM, which reads M_k as well but writes elsewhere.
+struct VecTask {
+  const __half* q;          // M_k's planes
+  size_t plane;
+  int ld, e, m, mp, p;
+  double c, alpha;
+  double* y;                // carried column of X (FP64)
+  float* u;                 // carried residual vector
+  float* yh;                // scratch: y as double-floats
+  float* yl;
+  double* my;               // scratch: M y
+  float* t;                 // scratch: M u
+};
+
+template <int BAR>
+__device__ void vec_task(const VecTask& v) {
+  const int gt = threadIdx.x, gn = grp_threads<BAR>();
+  for (int i = gt; i < v.mp; i += gn) {
+    float h = 0.f, l = 0.f;
+    if (i < v.m) split_dbl(v.y[i], h, l);
+    v.yh[i] = h;
+    v.yl[i] = l;
+  }
+  grp_sync<BAR>();
+  // M y (FP64) and M u (FP32) in one pass, then the other p - 1 products for u
+  matvec2_slices<2, BAR>(v.q, v.plane, v.ld, v.e, v.yh, v.yl, v.my, v.u, v.t, v.m, v.mp);
+  for (int i = gt; i < v.m; i += gn) v.y[i] = v.c * (v.alpha * v.y[i] - v.my[i]);
+  const float cf = (float)v.c, af = (float)v.alpha;
+  for (int t = 0; t < v.p; ++t) {
+    if (t > 0)
+      matvec_slices_f32<3, 4, BAR>(v.q, v.plane, v.ld, ldexpf(1.f, v.e - 7), v.u, v.t, v.m, v.mp);
+    for (int i = gt; i < v.m; i += gn) v.u[i] = cf * (af * v.u[i] - v.t[i]);
+    grp_sync<BAR>();
+  }
 }
 
 // Largest eigenvalue of the SPD X (power method, FP32, two leading planes).
@@ -282,9 +342,6 @@ __device__ float start_lo_slices(const __half* q, size_t plane, int ld, int e, i
 // 32 wide).  Five level accumulators of 48 columns make one 240-column TMEM buffer; two
 // buffers (480 of 512 columns) let the MMAs of tile t+1 run while the epilogue drains t.
 constexpr int TC_M = 128, TC_N = 48, TC_K = 32;        // tile and k-slice
-// CTAs per SM: two CTAs, each with half of TMEM and shared memory, let one CTA's
-// latency-bound phases (gather, vector steps) and epilogues overlap the other's MMAs.
-constexpr int TC_CTAS = 1;
 constexpr int TC_NBUF = TC_CTAS == 1 ? 2 : 1;          // TMEM accumulator buffers
 constexpr int TC_STAGES = TC_CTAS == 1 ? 3 : 2;
 constexpr int TC_A_PLANE = TC_M * TC_K * 2;            // 8192 B
@@ -297,7 +354,7 @@ constexpr uint32_t TC_TMEM_COLS = TC_CTAS == 1 ? 512 : 256;
 static_assert(TC_NBUF * TC_BUF_COLS <= (int)TC_TMEM_COLS, "TMEM budget");
 // tcgen05 CTA: warps 0-7 run the epilogue (warp w: TMEM lane quarter w % 4, column half
 // w / 4 of the tile), warp 8 issues TMA, warp 9 issues MMAs.
-constexpr int TC_EPI_WARPS = TC_CTAS == 1 ? 8 : 4;
+constexpr int TC_EPI_WARPS = kEpiGroupWarps;
 constexpr int TC_THREADS = (TC_EPI_WARPS + 2) * 32;
 constexpr int TC_TMA_WARP = TC_EPI_WARPS, TC_MMA_WARP = TC_EPI_WARPS + 1;
 constexpr int TC_EPI_COLS = TC_N * 4 / TC_EPI_WARPS;  // tile columns per epilogue warp
@@ -386,7 +443,7 @@ __device__ __forceinline__ unsigned store8_sym(__half* q, size_t plane, int ld, 
 // C = A B^T on the tcgen05 engine (see the header comment).  All TC_THREADS threads call it.
 // Returns false if a pipeline wait timed out (the CTA then stops).
 __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y, int flags,
-                        const GemmIO& io) {
+                        const GemmIO& io, const VecTask* vt) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mp = io.mp;
   const int ntm = (mp + TC_M - 1) / TC_M, ntn = (mp + TC_N - 1) / TC_N, KT = mp / TC_K;
@@ -476,6 +533,9 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
       }
     }
   } else {                                             // ---- epilogue (TMEM lanes 0..127)
+    // vector work handed to this GEMM: the MMA warp fills the first accumulator buffers
+    // meanwhile
+    if (vt) vec_task<kEpiBar>(*vt);
     const int q4 = warp & 3, half = warp >> 2;
     // the level sums count in units of cscale = 2^(A.e + B.e - 14), Y's planes in units of
     // 2^(Y.e - 15)
@@ -831,8 +891,13 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
     Mat B3[3] = {{hb + 2 * NSL * plane, e_m, plane_base + 10},
                  {hb + 3 * NSL * plane, e_m, plane_base + 15},
                  {hb + 4 * NSL * plane, e_m, plane_base + 20}};
-    double* yg = reinterpret_cast<double*>(hb + 34 * plane);     // tracked X_k e_pos (FP64)
-    float* ug = reinterpret_cast<float*>(yg + SUBMAT_MAX_M);     // tracked residual vector
+    // vectors carried for p >= 2 and their scratch, in the last plane (32 LD bytes)
+    double* yg = reinterpret_cast<double*>(hb + 34 * plane);     // column pos of X_k (FP64)
+    float* ug = reinterpret_cast<float*>(yg + LD);               // X_k^p M_0 e_pos
+    float* yhg = ug + LD;
+    float* ylg = yhg + LD;
+    double* myg = reinterpret_cast<double*>(ylg + LD);
+    float* tg = reinterpret_cast<float*>(myg + LD);
 
     const double lam = gather_submatrix(a.rowptr, a.colind, a.vals_in, j, m, R_s, S, red_s);
     const double inv_lam = 1.0 / lam;
@@ -880,51 +945,25 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
     // tracked vectors (p >= 2): y_0 = e_pos, u_0 = M_0 e_pos
     const bool track = (p >= 2);
     if (track) {
-      for (int i = tid; i < m; i += blockDim.x) {
+      for (int i = tid; i < mp; i += blockDim.x) {
         yg[i] = (i == pos) ? 1.0 : 0.0;
-        ug[i] = (float)(S[pos * m + i] * inv_lam);
+        ug[i] = i < m ? (float)(S[pos * m + i] * inv_lam) : 0.f;
       }
     }
     __threadfence();             // planes are read next through L2 (cp.async.cg / TMA)
     __syncthreads();
 
     GemmIO io{mp, m, p, LD, plane, norm2_s, amax_s, 0.f, 0.f};
-    auto gemm = [&](Mat A, Mat B, Mat C, Mat Y, int flags) -> bool {
-      if (TC) return gemm_tc(tcx, tst, A, B, C, Y, flags, io);
+    // vt: vector work to run with this GEMM (tcgen05: on the epilogue warps while the MMA
+    // warp starts; mma.sync: before the GEMM on all warps)
+    auto gemm = [&](Mat A, Mat B, Mat C, Mat Y, int flags, const VecTask* vt) -> bool {
+      if (TC) return gemm_tc(tcx, tst, A, B, C, Y, flags, io, vt);
+      if (vt) vec_task<0>(*vt);
       gemm_sync(A, B, C, Y, flags, io, reinterpret_cast<__half*>(sm));
       return true;
     };
-
-    // y <- c (alpha y - M y) in FP64 / double-float, u <- (c (alpha I - M))^p u in FP32:
-    // the step T = c (alpha I - M) applied to the tracked column and residual vectors.
-    float* yh_s = reinterpret_cast<float*>(v_s);                 // 2 x SUBMAT_MAX_M floats
-    float* yl_s = yh_s + SUBMAT_MAX_M;
-    float* u_s = reinterpret_cast<float*>(w_s);
-    float* t_s = u_s + SUBMAT_MAX_M;
-    double* my_s = reinterpret_cast<double*>(R_s + SUBMAT_MAX_M);
-    auto vec_step = [&](const Mat& Mk, double c, double alpha) {
-      for (int i = tid; i < mp; i += blockDim.x) {
-        const double yv = i < m ? yg[i] : 0.0;
-        y_s[i] = yv;
-        float h, l;
-        split_dbl(yv, h, l);
-        yh_s[i] = h;
-        yl_s[i] = l;
-        u_s[i] = i < m ? ug[i] : 0.f;
-        t_s[i] = 0.f;
-      }
-      __syncthreads();
-      // M y (FP64) and M u (FP32) in one pass, then the other p - 1 products for u
-      matvec2_slices(Mk.q, plane, LD, Mk.e, yh_s, yl_s, my_s, u_s, t_s, m, mp);
-      for (int i = tid; i < m; i += blockDim.x) yg[i] = c * (alpha * y_s[i] - my_s[i]);
-      const float cf = (float)c, af = (float)alpha;
-      for (int t = 0; t < p; ++t) {
-        if (t > 0) matvec_slices_f32<3>(Mk.q, plane, LD, ldexpf(1.f, Mk.e - 7), u_s, t_s, m, mp);
-        for (int i = tid; i < m; i += blockDim.x) u_s[i] = cf * (af * u_s[i] - t_s[i]);
-        __syncthreads();
-      }
-      for (int i = tid; i < m; i += blockDim.x) ug[i] = u_s[i];
-      __syncthreads();
+    auto vec_of = [&](const Mat& Mk, double c, double alpha) {
+      return VecTask{Mk.q, plane, LD, Mk.e, m, mp, p, c, alpha, yg, ug, yhg, ylg, myg, tg};
     };
 
     int xc = 0, mi = 0;
@@ -944,8 +983,9 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
       io.c = st.c;
       io.alpha = st.alpha;
       const Mat Mk = B3[mi];
+      const VecTask vt = vec_of(Mk, (double)st.c, (double)st.alpha);
       if (track) {
-        vec_step(Mk, (double)st.c, (double)st.alpha);
+        // the vector step runs with the first product below
       } else if (iters == 0) {
         // X_1 = T_0 (elementwise from M_0)
         X[0].e = exp_of(st.tmax) + eb;
@@ -972,7 +1012,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
         X[xc ^ 1].e = exp_of(xmax * st.tmax) + eb;
         if (tid == 0) *amax_s = 0u;
         __syncthreads();
-        if (!gemm(X[xc], Mk, X[xc ^ 1], X[xc], EPI_AMAX)) { stop = true; break; }
+        if (!gemm(X[xc], Mk, X[xc ^ 1], X[xc], EPI_AMAX, nullptr)) { stop = true; break; }
         ++n_gemm;
         xmax = __uint_as_float(*amax_s);
         xc ^= 1;
@@ -986,7 +1026,11 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
           if (tid == 0) *norm2_s = 0.f;
           __syncthreads();
         }
-        if (!gemm(Mk, B3[src], B3[dst], B3[src], last ? EPI_NORM : 0)) { stop = true; break; }
+        if (!gemm(Mk, B3[src], B3[dst], B3[src], last ? EPI_NORM : 0,
+                  (track && s == 1) ? &vt : nullptr)) {
+          stop = true;
+          break;
+        }
         ++n_gemm;
         src = dst;
         dst = 3 - mi - dst;                     // the buffer that is neither M_k nor P_s
@@ -1009,7 +1053,8 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
     float kest = 0.f;
     const double c = pow(lam, -1.0 / (double)p);
     if (!bad && track) {
-      vec_step(B3[mi], 1.0 / (double)p, (double)(p + 1));
+      __syncthreads();
+      vec_task<0>(vec_of(B3[mi], 1.0 / (double)p, (double)(p + 1)));
       // column pos of F = c X and the residual F^p s_pos - e_pos = u - e_pos
       float r = 0.f;
       for (int i = tid; i < m; i += blockDim.x) {
@@ -1031,7 +1076,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
       X[xc ^ 1].e = exp_of(xmax * 2.f) + eb;
       if (tid == 0) *amax_s = 0u;
       __syncthreads();
-      if (!gemm(X[xc], B3[mi], X[xc ^ 1], X[xc], EPI_AMAX)) break;
+      if (!gemm(X[xc], B3[mi], X[xc ^ 1], X[xc], EPI_AMAX, nullptr)) break;
       ++n_gemm;
       xc ^= 1;
       SliceLoad xl{X[xc].q, plane, LD, ldexp(1.0, X[xc].e - 7)};
