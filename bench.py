@@ -125,7 +125,11 @@ def make_workload(name, p, n=0):
     import workloads as wl
     if name not in wl.WORKLOADS:
         raise SystemExit(f"unknown workload {name}")
-    return wl.WORKLOADS[name](n=n) if n > 0 else wl.WORKLOADS[name]()
+    if n <= 0:
+        return wl.WORKLOADS[name]()
+    if name == "block_overlap":                     # n rows = 13 functions per atom
+        return wl.block_overlap(atoms=max(1, n // 13))
+    return wl.WORKLOADS[name](n=n)
 
 
 def clocks_start():

@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_fp64_kernel(FwdArgs a) {
       __syncthreads();
       if (!(nrm2 == nrm2) || nrm2 > 1e300) { bad = true; break; }
       if (nrm2 <= tol2 || iters >= a.k_max) break;
-      if (nrm2 <= stag2 && nrm2 > 0.25 * prev2) break;      // at the rounding-error floor
+      // at the rounding-error floor (only after a Newton step, as in the mixed path)
+      if (st.newton && nrm2 <= stag2 && nrm2 > 0.25 * prev2) break;
       prev2 = nrm2;
     }
     // last step: Newton's T = ((p+1) I - M)/p, whose first-order part is M^(-1/p)

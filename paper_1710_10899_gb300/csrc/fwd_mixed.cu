@@ -22,8 +22,9 @@
 // 2^(-8L) sum_{s+t=L} Q_s^A Q_t^B (15 FP16 MMAs per k-step, FP32 accumulation per level).
 // The products of these integers are exact, and every level-0 partial sum is an integer
 // below 2^14 K, so for K <= 1024 the tensor cores accumulate level 0 exactly (level 1
-// below 2^15 K: exact for K <= 512, and its weight is 2^-8 anyway); levels 2..4 carry
-// weights 2^-16..2^-32.  Orders above 1024 raise every exponent by one (|q0| <= 64).  The levels dropped (s + t >= 5) bound the normwise error of a
+// multiplies q0 by a residual slice of either sign: its sums stay far below 2^24 in practice,
+// and its weight is 2^-8); levels 2..4 carry weights 2^-16..2^-32.  Orders above 1024 raise
+// every exponent by one (exp_bias), which keeps level 0 exact up to K = 4096.  The levels dropped (s + t >= 5) bound the normwise error of a
 // product near 2^-39 sqrt(K) of max|A| max|B|.  The epilogue combines the levels in
 // double-float (FP32 pairs) and re-splits the result.  (With four planes, the ~2^-31
 // per-product error, kept by every iteration, left ~6e-7 in the result; measured.)
@@ -84,7 +85,9 @@ struct GemmIO {     // what every GEMM call shares within one submatrix
 __device__ __forceinline__ int exp_of(float b) { return exp_bound(b * (1.f + 1e-6f)); }
 
 // Extra exponent for orders above 1024: with |q0| <= 64 every level-0 partial sum stays an
-// integer below 2^12 K < 2^24 up to K = 4096 (one of the 39 bits is given up).
+// integer below 2^12 K < 2^24 up to K = 4096 (one of the ~39 bits is given up).  Level 0
+// matters most: for same-sign data (overlap matrices) its sums grow linearly with K, while
+// level 1 multiplies q0 by a rounding residual of either sign and grows like sqrt(K).
 __device__ __forceinline__ int exp_bias(int mp) { return mp > 1024 ? 1 : 0; }
 
 // Slices of 8 consecutive values -> one 16-byte store per plane.
@@ -1043,7 +1046,9 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
       __syncthreads();
       if (!(nrm2 == nrm2) || nrm2 > 1e30f) { bad = true; break; }
       if (nrm2 <= tol2 || iters >= a.k_max) break;
-      if (nrm2 <= stag2 && nrm2 > 0.25f * prev2) break;     // at the rounding-error floor
+      // at the rounding-error floor (only after a Newton step: a scaled step maps the
+      // interval's upper end below 1 and may shrink the norm less while converging fast)
+      if (st.newton && nrm2 <= stag2 && nrm2 > 0.25f * prev2) break;
       prev2 = nrm2;
     }
     if (stop) break;

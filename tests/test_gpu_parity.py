@@ -134,6 +134,33 @@ def test_dense_pattern_equals_full_root(sm):
     assert np.abs(yd - full.T).max() / np.abs(full).max() < 1e-6
 
 
+def test_clustered_uneven_sizes(sm):
+    # the uneven-batching workload at 1/8 scale (orders 10..596): the largest and smallest
+    # rows and a random sample against the oracle (orders above 1024: test_order_above_1024)
+    a = wl.overlap_clustered(n=16384)
+    m = a.row_sizes()
+    plan, y = run(sm, a, 2, "mixed")
+    order = np.argsort(m)
+    rows = sorted(set(order[-4:].tolist()) | set(order[:2].tolist()) | set(sample_rows(a, 20, seed=5)))
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, 2, rows=rows)
+    assert m.max() > 4 * m.min()
+    assert row_errors(a, y, ref, rows).max() <= TOL["mixed"]
+
+
+def test_block_overlap_sampled(sm):
+    # the block-sparse Gaussian-basis workload at 800 atoms (n = 10400, orders 546..1235,
+    # so the largest rows also take the exponent bias of orders above 1024)
+    a = wl.block_overlap(atoms=800)
+    m = a.row_sizes()
+    plan, y = run(sm, a, 2, "mixed")
+    order = np.argsort(m)
+    rows = sorted(set(order[-3:].tolist()) | {int(order[0])} | set(sample_rows(a, 8, seed=6)))
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, 2, rows=rows)
+    assert m.max() > 1024
+    assert row_errors(a, y, ref, rows).max() <= TOL["mixed"]
+    assert plan.report()["n_fallback"] == 0
+
+
 @pytest.mark.parametrize("p", [1, 2])
 def test_order_above_1024(sm, p):
     # arrow + band: row 0's submatrix is the whole 1200 x 1200 matrix (padded order 1216),

@@ -21,6 +21,12 @@ Recipes (numpy PCG64, seed 0 unless stated):
   64 isotropic Gaussian clusters (std 0.1), 15 % uniform; minimum-image distances;
   kappa ~ 1e3.  Row sizes range 7..1113.
 * ``overlap_grad`` n=16384 points U[0,0.9247]^3 (about 130 entries per row), kappa ~ 1e3.
+* ``block_overlap`` 20000 atoms U[0,1]^3 (periodic) with 13 s-type Gaussian functions
+  each (n = 260000): dense 13 x 13 blocks between atoms closer than the cutoff
+  r_c = (64 / (20000 * 4/3 pi))^(1/3) (65 neighbour atoms including the atom itself);
+  block entries are the overlaps of normalised Gaussians with exponents geometric in
+  0.5 .. 8 r_c^-2, (2 sqrt(a b) / (a + b))^(3/2) exp(-a b / (a + b) r^2); diagonal shift
+  to kappa ~ 1e4.  Submatrix orders are 13 x (number of neighbour atoms), ~845 on average.
 
 Every generator can also be scaled down (``n=``) for fast tests; the box side is then
 rescaled so the expected number of neighbours stays the same.
@@ -185,9 +191,51 @@ def random_on_pattern(a: CSR, seed: int, symmetric: bool = False) -> np.ndarray:
     return w
 
 
+def block_overlap(atoms: int = 20000, funcs: int = 13, seed: int = 0,
+                  kappa: float = 1e4) -> CSR:
+    """Block-sparse Gaussian-basis overlap matrix (n = atoms * funcs), see the module doc."""
+    rng = np.random.default_rng(seed)
+    rc = (64.0 / (20000 * 4.0 / 3.0 * np.pi)) ** (1.0 / 3.0)
+    side = (atoms / 20000.0) ** (1.0 / 3.0)            # same atom density at any size
+    pos = rng.uniform(0.0, side, (atoms, 3))
+    tree = scipy.spatial.cKDTree(pos, boxsize=side)
+    pairs = tree.query_pairs(rc, output_type="ndarray").astype(np.int64)
+    d = pos[pairs[:, 0]] - pos[pairs[:, 1]]
+    d -= side * np.round(d / side)
+    r2 = (d * d).sum(1)
+    alpha = 0.5 * 16.0 ** (np.arange(funcs) / (funcs - 1)) / rc ** 2
+    prod = alpha[:, None] * alpha[None, :]
+    tot = alpha[:, None] + alpha[None, :]
+    pref = (2.0 * np.sqrt(prod) / tot) ** 1.5
+    red = prod / tot
+    f = np.arange(funcs)
+    # off-diagonal blocks (a < b) and their transposes, then the diagonal blocks (r = 0)
+    blk = pref[None] * np.exp(-red[None] * r2[:, None, None])
+    ia = (pairs[:, 0, None, None] * funcs + f[None, :, None]) + 0 * f[None, None, :]
+    jb = (pairs[:, 1, None, None] * funcs + f[None, None, :]) + 0 * f[None, :, None]
+    ad = np.arange(atoms)
+    id_ = (ad[:, None, None] * funcs + f[None, :, None]) + 0 * f[None, None, :]
+    jd_ = (ad[:, None, None] * funcs + f[None, None, :]) + 0 * f[None, :, None]
+    n = atoms * funcs
+    i = np.concatenate([ia.ravel(), jb.ravel(), id_.ravel()])
+    j = np.concatenate([jb.ravel(), ia.ravel(), jd_.ravel()])
+    v = np.concatenate([blk.ravel(), blk.ravel(), np.broadcast_to(pref, (atoms, funcs, funcs)).ravel()])
+    g = sp.csr_matrix((v, (i, j)), shape=(n, n))
+    g.sum_duplicates()
+    v0 = np.random.default_rng(seed).standard_normal(n)
+    hi = sla.eigsh(g, k=1, which="LA", v0=v0, tol=1e-8, return_eigenvectors=False)[0]
+    lo = hi - sla.eigsh(hi * sp.identity(n, format="csr") - g, k=1, which="LA", v0=v0,
+                        tol=1e-8, return_eigenvectors=False)[0]
+    g = (g + diag_for_kappa(float(lo), float(hi), kappa) * sp.identity(n, format="csr")).tocsr()
+    g.sort_indices()
+    return CSR(n, g.indptr.astype(np.int32), g.indices.astype(np.int32),
+               g.data.astype(np.float64), f"block_overlap(atoms={atoms},funcs={funcs},kappa={kappa:g})")
+
+
 WORKLOADS = {
     "overlap_small": overlap_small,
     "overlap_uniform": overlap_uniform,
     "overlap_clustered": overlap_clustered,
     "overlap_grad": overlap_grad,
+    "block_overlap": block_overlap,
 }
