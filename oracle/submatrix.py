@@ -18,6 +18,8 @@ What it computes, in the paper's order:
 * Algorithm 2 (Sec. 3.3) with the row-based storage of Sec. 3.4: row j of the CSR
   result holds column R.indexof(j) of f(S_j), in the order of R, i.e. the result
   reuses A's rowptr/colind and only the value array is new.
+* Sec. 4.2 applies the same method to positive p-th roots; every function below takes
+  ``sign=-1`` (the default, f(S) = S^(-1/p)) or ``sign=+1`` (f(S) = S^(1/p)).
 
 Readings where the paper is silent (each also listed in the design notes):
 
@@ -86,28 +88,28 @@ def submatrix(rowptr, colind, vals, j):
 # Sec. 3.2: the submatrix operation
 # ---------------------------------------------------------------------------
 
-def inv_root(s, p):
-    """S^(-1/p) of a symmetric positive definite S via its eigendecomposition."""
+def inv_root(s, p, sign=-1):
+    """S^(sign/p) of a symmetric positive definite S via its eigendecomposition."""
     lam, v = np.linalg.eigh(s)
     if lam[0] <= 0.0:
         raise ValueError(f"submatrix not positive definite (lambda_min = {lam[0]:.3e})")
-    return (v * lam ** (-1.0 / p)) @ v.T
+    return (v * lam ** (sign / p)) @ v.T
 
 
-def inv_root_column(s, pos, p):
-    """Column pos of S^(-1/p) (the only column Alg. 2 keeps)."""
+def inv_root_column(s, pos, p, sign=-1):
+    """Column pos of S^(sign/p) (the only column Alg. 2 keeps)."""
     lam, v = np.linalg.eigh(s)
     if lam[0] <= 0.0:
         raise ValueError(f"submatrix not positive definite (lambda_min = {lam[0]:.3e})")
-    return v @ (lam ** (-1.0 / p) * v[pos, :])
+    return v @ (lam ** (sign / p) * v[pos, :])
 
 
 # ---------------------------------------------------------------------------
 # Alg. 1 + Sec. 3.2 + Alg. 2: the whole method
 # ---------------------------------------------------------------------------
 
-def invroot(rowptr, colind, vals, p, rows=None):
-    """The submatrix method's approximation of A^(-1/p) on A's CSR pattern.
+def invroot(rowptr, colind, vals, p, rows=None, sign=-1):
+    """The submatrix method's approximation of A^(sign/p) on A's CSR pattern.
 
     Returns the value array of the result (length nnz; same rowptr/colind as A).
     With ``rows`` given, only those rows' segments are computed and the rest of the
@@ -117,38 +119,39 @@ def invroot(rowptr, colind, vals, p, rows=None):
     n = len(rowptr) - 1
     for j in (range(n) if rows is None else rows):
         s, r, pos = submatrix(rowptr, colind, vals, j)
-        out[rowptr[j]:rowptr[j + 1]] = inv_root_column(s, pos, p)
+        out[rowptr[j]:rowptr[j + 1]] = inv_root_column(s, pos, p, sign)
     return out
 
 
-def row_segment(rowptr, colind, vals, p, j):
-    """Row j of the result alone (column pos_j of S_j^(-1/p))."""
+def row_segment(rowptr, colind, vals, p, j, sign=-1):
+    """Row j of the result alone (column pos_j of S_j^(sign/p))."""
     s, r, pos = submatrix(rowptr, colind, vals, j)
-    return inv_root_column(s, pos, p)
+    return inv_root_column(s, pos, p, sign)
 
 
 # ---------------------------------------------------------------------------
 # Gradient of a loss on the result with respect to A's stored values
 # ---------------------------------------------------------------------------
 
-def divided_differences(lam, p):
-    """Gamma_ab = (f(l_a) - f(l_b)) / (l_a - l_b) for f(l) = l^(-1/p), Gamma_aa = f'(l_a).
+def divided_differences(lam, p, sign=-1):
+    """Gamma_ab = (f(l_a) - f(l_b)) / (l_a - l_b) for f(l) = l^(sign/p), Gamma_aa = f'(l_a).
 
-    With a = l^(1/p):  f(l_a) - f(l_b) = (a_b - a_a)/(a_a a_b) and
-    l_a - l_b = (a_a - a_b) sum_{i<p} a_a^i a_b^(p-1-i), so the quotient is
-    -1 / (a_a a_b sum_i a_a^i a_b^(p-1-i)), which has no cancellation and equals
-    f'(l) = -(1/p) l^(-1/p-1) on the diagonal."""
+    With a = l^(1/p):  l_a - l_b = (a_a - a_b) sum_{i<p} a_a^i a_b^(p-1-i).  For
+    f(l) = l^(-1/p), f(l_a) - f(l_b) = (a_b - a_a)/(a_a a_b), so the quotient is
+    -1 / (a_a a_b sum_i a_a^i a_b^(p-1-i)); for f(l) = l^(1/p) it is
+    1 / sum_i a_a^i a_b^(p-1-i).  Neither has cancellation, and on the diagonal they equal
+    f'(l) = -(1/p) l^(-1/p-1) and (1/p) l^(1/p-1)."""
     a = lam ** (1.0 / p)
     aa = a[:, None]
     bb = a[None, :]
     ssum = np.zeros((len(a), len(a)))
     for i in range(p):
         ssum += aa ** i * bb ** (p - 1 - i)
-    return -1.0 / (aa * bb * ssum)
+    return 1.0 / ssum if sign > 0 else -1.0 / (aa * bb * ssum)
 
 
-def submatrix_grad(s, pos, g, p):
-    """dL/dS for L = <g, column pos of S^(-1/p)>, symmetrised (Daleckii-Krein)."""
+def submatrix_grad(s, pos, g, p, sign=-1):
+    """dL/dS for L = <g, column pos of S^(sign/p)>, symmetrised (Daleckii-Krein)."""
     lam, v = np.linalg.eigh(s)
     if lam[0] <= 0.0:
         raise ValueError("submatrix not positive definite")
@@ -156,12 +159,12 @@ def submatrix_grad(s, pos, g, p):
     gbar = np.zeros((m, m))
     gbar[:, pos] += 0.5 * g
     gbar[pos, :] += 0.5 * g
-    gam = divided_differences(lam, p)
+    gam = divided_differences(lam, p, sign)
     return v @ (gam * (v.T @ gbar @ v)) @ v.T
 
 
-def grad(rowptr, colind, vals, p, grad_out):
-    """Gradient of L = sum(grad_out * invroot(A)) with respect to A's stored values.
+def grad(rowptr, colind, vals, p, grad_out, sign=-1):
+    """Gradient of L = sum(grad_out * invroot(A, sign)) with respect to A's stored values.
 
     For every row j: G_j = dL/dS_j (``submatrix_grad``), then G_j[k][l] is added to the
     stored value at (R_j[k], R_j[l]).  Entries of S_j that are not stored in A are
@@ -170,7 +173,7 @@ def grad(rowptr, colind, vals, p, grad_out):
     out = np.zeros(len(colind))
     for j in range(n):
         s, r, pos = submatrix(rowptr, colind, vals, j)
-        gj = submatrix_grad(s, pos, np.asarray(grad_out[rowptr[j]:rowptr[j + 1]]), p)
+        gj = submatrix_grad(s, pos, np.asarray(grad_out[rowptr[j]:rowptr[j + 1]]), p, sign)
         for k in range(len(r)):
             row = r[k]
             cols = np.asarray(colind[rowptr[row]:rowptr[row + 1]], dtype=np.int64)

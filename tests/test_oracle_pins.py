@@ -261,3 +261,80 @@ def test_grad_central_differences(p):
     # symmetric: the (r,c) and (c,r) entries carry the same value
     d = oracle.to_dense(a.n, a.rowptr, a.colind, gr)
     np.testing.assert_allclose(d, d.T, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Positive p-th roots (Sec. 4.2): the same method with f(S) = S^(1/p)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_positive_root_dense_pattern_is_full_root(p):
+    a = _dense_spd(24, seed=40 + p)
+    csr = wl.dense_to_csr(a, keep=np.ones_like(a, dtype=bool))
+    y = oracle.invroot(csr.rowptr, csr.colind, csr.vals, p, sign=1)
+    full = np.real(sl.fractional_matrix_power(a, 1.0 / p))
+    ydense = oracle.to_dense(csr.n, csr.rowptr, csr.colind, y)
+    np.testing.assert_allclose(ydense, full.T, rtol=0, atol=1e-12)
+
+
+def test_positive_root_p1_returns_the_stored_values():
+    a = wl.overlap_small(n=300)
+    y = oracle.invroot(a.rowptr, a.colind, a.vals, 1, sign=1)
+    np.testing.assert_allclose(y, a.vals, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_positive_root_diagonal_and_2x2(p):
+    d = np.array([0.5, 2.0, 3.0, 10.0, 1e-3])
+    csr = wl.dense_to_csr(np.diag(d))
+    np.testing.assert_allclose(oracle.invroot(csr.rowptr, csr.colind, csr.vals, p, sign=1),
+                               d ** (1.0 / p), rtol=1e-14)
+    if p == 2:
+        # sqrt of a 2x2 SPD matrix: (M + sqrt(det) I) / sqrt(tr + 2 sqrt(det))
+        m2 = np.array([[2.0, 0.7], [0.7, 1.5]])
+        sd = np.sqrt(np.linalg.det(m2))
+        expect = (m2 + sd * np.eye(2)) / np.sqrt(np.trace(m2) + 2.0 * sd)
+        csr2 = wl.dense_to_csr(m2)
+        y = oracle.to_dense(2, csr2.rowptr, csr2.colind,
+                            oracle.invroot(csr2.rowptr, csr2.colind, csr2.vals, 2, sign=1))
+        np.testing.assert_allclose(y, expect.T, atol=1e-15)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_positive_root_submatrix_relations(p):
+    # on every submatrix: (S^(1/p))^p = S, and column pos of S^(1/p) = S (S^(-1/p))^(p-1) e_pos
+    a = wl.random_sparse_spd(40, 0.15, seed=8)
+    for j in range(a.n):
+        s, r, pos = oracle.submatrix(a.rowptr, a.colind, a.vals, j)
+        f = oracle.inv_root(s, p, sign=1)
+        np.testing.assert_allclose(np.linalg.matrix_power(f, p), s, atol=1e-12 * np.abs(s).max())
+        e = np.zeros(len(r))
+        e[pos] = 1.0
+        g = np.linalg.matrix_power(np.real(sl.fractional_matrix_power(s, -1.0 / p)), p - 1) @ e
+        np.testing.assert_allclose(oracle.inv_root_column(s, pos, p, sign=1), s @ g, atol=1e-12)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_positive_root_grad_frechet_and_central_differences(p):
+    rng = np.random.default_rng(30 + p)
+    m = 7
+    s = _dense_spd(m, seed=p, shift=0.7)
+    g = rng.standard_normal(m)
+    e = rng.standard_normal((m, m))
+    e = e + e.T
+    z = np.block([[s, e], [np.zeros((m, m)), s]])
+    lf = np.real(sl.fractional_matrix_power(z, 1.0 / p))[:m, m:]
+    lhs = np.sum(oracle.submatrix_grad(s, 2, g, p, sign=1) * e)
+    assert abs(lhs - g @ lf[:, 2]) < 1e-11 * max(1.0, abs(lhs))
+    a = wl.overlap_uniform(n=200, kappa=50.0)
+    w = wl.random_on_pattern(a, seed=1)
+    gr = oracle.grad(a.rowptr, a.colind, a.vals, p, w, sign=1)
+
+    def loss(v):
+        return float(np.dot(w, oracle.invroot(a.rowptr, a.colind, v, p, sign=1)))
+
+    h = 1e-6
+    d = wl.random_on_pattern(a, seed=200, symmetric=True)
+    d /= np.linalg.norm(d)
+    fd = (loss(a.vals + h * d) - loss(a.vals - h * d)) / (2 * h)
+    assert abs(fd - gr @ d) <= 1e-6 * max(1.0, abs(fd))
