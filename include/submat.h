@@ -88,6 +88,11 @@ typedef struct {
   double kappa_max;        /* mixed path: a row whose condition estimate
                               lambda_bar / lambda_min (power iteration on the converged
                               iterate) exceeds this goes to the FP64 fallback; default 100 */
+  int32_t root_sign;       /* -1 (default): the inverse p-th root A^(-1/p); +1: the positive
+                              p-th root A^(1/p), the same method with f(S) = S^(1/p)
+                              (Sec. 4.2), computed from the same iteration as
+                              S^(1/p) e_pos = S (S^(-1/p))^(p-1) e_pos; any other value is
+                              SUBMAT_EINVAL.  submat_invroot_noalloc is inverse only.     */
 } submat_opts;
 
 typedef struct {
@@ -125,8 +130,8 @@ SUBMAT_API submat_status submat_plan(const submat_csr* csr, int32_t p, const sub
                           submat_plan_t* out);
 
 /*
- * Forward: vals_out = the submatrix method's approximation of A^(-1/p) on A's pattern
- * (Alg. 1, Sec. 3.2, Alg. 2).  vals_in and vals_out are device arrays of nnz doubles in
+ * Forward: vals_out = the submatrix method's approximation of A^(-1/p) (A^(1/p) with
+ * root_sign = +1) on A's pattern (Alg. 1, Sec. 3.2, Alg. 2).  vals_in and vals_out are device arrays of nnz doubles in
  * CSR order; they must not overlap.  A's values must be symmetric (A[r][c] = A[c][r]).
  * The plan keeps a device copy of vals_in for the backward.  Returns SUBMAT_ENOTSPD (after
  * writing every other row) when some submatrix is not positive definite.  Stream-ordered;
@@ -148,7 +153,8 @@ SUBMAT_API submat_status submat_invroot_host(submat_plan_t plan, const double* v
                                              double* vals_out, void* stream);
 
 /*
- * Backward (Daleckii-Krein adjoint; Higham, Functions of Matrices, Thm. 3.11):
+ * Backward (Daleckii-Krein adjoint; Higham, Functions of Matrices, Thm. 3.11, with
+ * f(x) = x^(root_sign/p)):
  * grad_in = dL/dvals for L = sum(grad_out * vals_out) of the last forward, with respect to
  * A's stored values, the (r,c)/(c,r) pair sharing one symmetric perturbation.  For each row
  * j the submatrix is regathered from the saved vals_in and decomposed again in FP64

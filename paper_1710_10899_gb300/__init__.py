@@ -50,7 +50,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("k_max", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("resid_tol", ctypes.c_double),
                 ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("kappa_max", ctypes.c_double)]
+                ("kappa_max", ctypes.c_double), ("root_sign", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -133,7 +133,7 @@ class Plan:
 
     def __init__(self, rowptr, colind, p: int, precision: str = "mixed", k_max: int = 0,
                  tol: float = 0.0, resid_tol: float = 0.0, refine_steps: int = -1,
-                 use_graph: bool = True, kappa_max: float = 0.0):
+                 use_graph: bool = True, kappa_max: float = 0.0, root_sign: int = -1):
         lib = load_library()
         self._lib = lib
         torch = _torch()
@@ -162,6 +162,7 @@ class Plan:
         o.refine_steps = refine_steps
         o.use_graph = 1 if use_graph else 0
         o.kappa_max = kappa_max
+        o.root_sign = int(root_sign)
         h = ctypes.c_void_p()
         _check(lib, lib.submat_plan(ctypes.byref(csr), int(p), ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -169,6 +170,7 @@ class Plan:
         self.nnz = int(nnz)
         self.p = int(p)
         self.precision = precision
+        self.root_sign = int(root_sign)
         self.device = torch.device("cuda", torch.cuda.current_device())
 
     def __del__(self):

@@ -135,6 +135,7 @@ submat_status enqueue_forward(submat_plan_t P, const double* in, double* out, cu
   a.resid_tol = P->opts.resid_tol;
   a.refine_steps = P->opts.refine_steps;
   a.kappa_max = P->opts.kappa_max;
+  a.sign = P->opts.root_sign;
   a.ld = P->ld;
   a.engine = P->opts.precision == SUBMAT_PREC_MIXED_F16_SYNC ? 1 : 0;
   a.tm_a = P->tm_a;
@@ -166,6 +167,7 @@ void submat_default_opts(submat_opts* o) {
   o->refine_steps = -1;
   o->use_graph = 1;
   o->kappa_max = 100.0;
+  o->root_sign = -1;
 }
 
 const char* submat_status_string(submat_status s) {
@@ -209,6 +211,7 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   if (!(o.resid_tol > 0.0)) o.resid_tol = 1e-3;
   if (o.refine_steps < 0) o.refine_steps = (p == 1) ? 2 : 0;
   if (!(o.kappa_max > 0.0)) o.kappa_max = 100.0;
+  if (o.root_sign != -1 && o.root_sign != 1) return fail(SUBMAT_EINVAL, "root_sign must be -1 or +1");
 
   const int32_t n = csr->n;
   const int64_t nnz = csr->nnz;
@@ -464,6 +467,7 @@ submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, d
   a.ctr = P->d_ctr_bwd;
   a.scratch = P->d_scratch;
   a.scratch_stride = P->stride;
+  a.sign = P->opts.root_sign;
   CUDA_TRY(cudaMemsetAsync(grad_in, 0, (size_t)P->nnz * sizeof(double), s));
   CUDA_TRY(cudaMemsetAsync(P->d_ctr_bwd, 0, sizeof(DevCounters), s));
   CUDA_TRY(launch_backward(a, P->grid, s));

@@ -56,6 +56,7 @@ struct FwdArgs {
   double resid_tol;
   int32_t refine_steps;
   double kappa_max;
+  int32_t sign;              // -1: A^(-1/p), +1: A^(1/p)
 };
 
 struct BwdArgs {
@@ -72,6 +73,7 @@ struct BwdArgs {
   DevCounters* ctr;
   char* scratch;
   size_t scratch_stride;
+  int32_t sign;              // -1: A^(-1/p), +1: A^(1/p)
 };
 
 // Launchers (return cudaGetLastError() of the launch).

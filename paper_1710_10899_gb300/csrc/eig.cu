@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kThreads) fallback_kernel(FwdArgs a) {
     for (int i = tid; i < m; i += blockDim.x) {
       const double l = A[i * m + i];
       if (!(l > 0.0) || !(l < 1e308)) bad_s = 1;
-      lam_s[i] = pow(l, -1.0 / (double)p) * V[pos * m + i];
+      lam_s[i] = pow(l, (double)a.sign / (double)p) * V[pos * m + i];   // f(l) = l^(sign/p)
     }
     __syncthreads();
     double* out = a.vals_out + a.rowptr[j];
@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
         ssum += px * py;
         px *= ax;
       }
-      const double gam = -1.0 / (ax * ay * ssum);
+      // divided difference of f(l) = l^(sign/p) in the eigenvalues' p-th roots ax, ay
+      const double gam = a.sign > 0 ? 1.0 / ssum : -1.0 / (ax * ay * ssum);
       A[e] = gam * 0.5 * (u_s[x] * w_s[y] + w_s[x] * u_s[y]);
     }
     __syncthreads();

@@ -65,20 +65,24 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_fp64_kernel(FwdArgs a) {
     double nrm2 = *norm2_s;
     float lo = 0.5f * start_lo(S, m, inv_lam, v_s, w_s, red_s, kStartLoSteps);
 
-    // tracked vectors (p >= 2): y = X_k e_pos in y_s, u = X_k^p M_0 e_pos in v_s
+    // tracked vectors (p >= 2): y = X_k e_pos (A^(-1/p)) or X_k^(p-1) M_0 e_pos (A^(1/p)) in
+    // y_s, u = X_k^p M_0 e_pos in v_s
     const bool track = (p >= 2);
+    const int ny = a.sign < 0 ? 1 : p - 1;
     if (track) {
       for (int i = tid; i < m; i += blockDim.x) {
-        y_s[i] = (i == pos) ? 1.0 : 0.0;
         v_s[i] = S[pos * m + i] * inv_lam;
+        y_s[i] = a.sign < 0 ? ((i == pos) ? 1.0 : 0.0) : v_s[i];
       }
     }
     __syncthreads();
     auto vec_step = [&](const double* Mk, double c, double alpha) {
       DenseLoad Ml{Mk, mp};
-      matvec_rows(Ml, 1.0, y_s, w_s, m);
-      for (int i = tid; i < m; i += blockDim.x) y_s[i] = c * (alpha * y_s[i] - w_s[i]);
-      __syncthreads();
+      for (int t = 0; t < ny; ++t) {
+        matvec_rows(Ml, 1.0, y_s, w_s, m);
+        for (int i = tid; i < m; i += blockDim.x) y_s[i] = c * (alpha * y_s[i] - w_s[i]);
+        __syncthreads();
+      }
       for (int t = 0; t < p; ++t) {
         matvec_rows(Ml, 1.0, v_s, w_s, m);
         for (int i = tid; i < m; i += blockDim.x) v_s[i] = c * (alpha * v_s[i] - w_s[i]);
@@ -139,9 +143,10 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_fp64_kernel(FwdArgs a) {
     const double cl = pow(lam, -1.0 / (double)p);
     if (!bad && track) {
       vec_step(B3[mi], 1.0 / (double)p, (double)(p + 1));
+      const double c_out = a.sign < 0 ? cl : pow(lam, 1.0 / (double)p);
       for (int i = tid; i < m; i += blockDim.x) {
         w_s[i] = v_s[i] - (i == pos ? 1.0 : 0.0);
-        y_s[i] *= cl;
+        y_s[i] *= c_out;
       }
       __syncthreads();
       resid = block_norm2(w_s, m, red_s);                    // ||F^p s_pos - e_pos||
@@ -151,6 +156,10 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_fp64_kernel(FwdArgs a) {
       xc ^= 1;
       DenseLoad xl{X[xc], mp};
       resid = refine_column(xl, cl, S, m, pos, p, a.refine_steps, y_s, v_s, w_s, red_s);
+      if (a.sign > 0) {          // A^(1/1): column pos of S itself (the iteration still checks S)
+        for (int i = tid; i < m; i += blockDim.x) y_s[i] = S[pos * m + i];
+        __syncthreads();
+      }
     }
     const bool ok = !bad && (resid <= a.resid_tol);
     if (ok) {

@@ -234,8 +234,8 @@ __device__ void matvec2_slices(const __half* q, size_t plane, int ld, int e, con
   grp_sync<BAR>();
 }
 
-// The step T = c (alpha I - M_k) applied to the vectors carried for p >= 2: y <- T y (FP64
-// result of a double-float product), u <- T^p u (FP32).  All vectors live in the CTA's
+// The step T = c (alpha I - M_k) applied to the vectors carried for p >= 2: y <- T^ny y (FP64
+// results of double-float products), u <- T^p u (FP32).  All vectors live in the CTA's
 // global scratch and are zero beyond m up to mp.  Run by a warp group (BAR, see grp_sync):
 // inside the tcgen05 engine the epilogue warps do it while the MMA warp starts the
 // iteration's first GEMM, which reads M_k as well but writes elsewhere.
@@ -243,6 +243,7 @@ struct VecTask {
   const __half* q;          // M_k's planes
   size_t plane;
   int ld, e, m, mp, p;
+  int ny;                   // applications of T to y: 1 (A^(-1/p)) or p - 1 (A^(1/p))
   double c, alpha;
   double* y;                // carried column of X (FP64)
   float* u;                 // carried residual vector
@@ -255,20 +256,22 @@ struct VecTask {
 template <int BAR>
 __device__ void vec_task(const VecTask& v) {
   const int gt = threadIdx.x, gn = grp_threads<BAR>();
-  for (int i = gt; i < v.mp; i += gn) {
-    float h = 0.f, l = 0.f;
-    if (i < v.m) split_dbl(v.y[i], h, l);
-    v.yh[i] = h;
-    v.yl[i] = l;
-  }
-  grp_sync<BAR>();
-  // M y (FP64) and M u (FP32) in one pass, then the other p - 1 products for u
-  matvec2_slices<2, BAR>(v.q, v.plane, v.ld, v.e, v.yh, v.yl, v.my, v.u, v.t, v.m, v.mp);
-  for (int i = gt; i < v.m; i += gn) v.y[i] = v.c * (v.alpha * v.y[i] - v.my[i]);
   const float cf = (float)v.c, af = (float)v.alpha;
   for (int t = 0; t < v.p; ++t) {
-    if (t > 0)
+    if (t < v.ny) {
+      // M y (FP64) and M u (FP32) in one pass
+      for (int i = gt; i < v.mp; i += gn) {
+        float h = 0.f, l = 0.f;
+        if (i < v.m) split_dbl(v.y[i], h, l);
+        v.yh[i] = h;
+        v.yl[i] = l;
+      }
+      grp_sync<BAR>();
+      matvec2_slices<2, BAR>(v.q, v.plane, v.ld, v.e, v.yh, v.yl, v.my, v.u, v.t, v.m, v.mp);
+      for (int i = gt; i < v.m; i += gn) v.y[i] = v.c * (v.alpha * v.y[i] - v.my[i]);
+    } else {
       matvec_slices_f32<3, 4, BAR>(v.q, v.plane, v.ld, ldexpf(1.f, v.e - 7), v.u, v.t, v.m, v.mp);
+    }
     for (int i = gt; i < v.m; i += gn) v.u[i] = cf * (af * v.u[i] - v.t[i]);
     grp_sync<BAR>();
   }
@@ -947,10 +950,14 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
 
     // tracked vectors (p >= 2): y_0 = e_pos, u_0 = M_0 e_pos
     const bool track = (p >= 2);
+    // A^(-1/p): y_0 = e_pos and y <- T y per step; A^(1/p): y_0 = M_0 e_pos and
+    // y <- T^(p-1) y, since S^(1/p) e_pos = lambda_bar^(1/p) X^(p-1) M_0 e_pos at the limit
+    const int ny = a.sign < 0 ? 1 : p - 1;
     if (track) {
       for (int i = tid; i < mp; i += blockDim.x) {
-        yg[i] = (i == pos) ? 1.0 : 0.0;
-        ug[i] = i < m ? (float)(S[pos * m + i] * inv_lam) : 0.f;
+        const double s0 = i < m ? S[pos * m + i] * inv_lam : 0.0;
+        yg[i] = a.sign < 0 ? ((i == pos) ? 1.0 : 0.0) : s0;
+        ug[i] = (float)s0;
       }
     }
     __threadfence();             // planes are read next through L2 (cp.async.cg / TMA)
@@ -966,7 +973,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
       return true;
     };
     auto vec_of = [&](const Mat& Mk, double c, double alpha) {
-      return VecTask{Mk.q, plane, LD, Mk.e, m, mp, p, c, alpha, yg, ug, yhg, ylg, myg, tg};
+      return VecTask{Mk.q, plane, LD, Mk.e, m, mp, p, ny, c, alpha, yg, ug, yhg, ylg, myg, tg};
     };
 
     int xc = 0, mi = 0;
@@ -1056,14 +1063,17 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
     // last step: Newton's T = ((p+1) I - M)/p, whose first-order part is M^(-1/p)
     double resid = 1e300;
     float kest = 0.f;
-    const double c = pow(lam, -1.0 / (double)p);
+    const double c = pow(lam, -1.0 / (double)p);               // F = c X
     if (!bad && track) {
+      const double c_out = a.sign < 0 ? c : pow(lam, 1.0 / (double)p);
       __syncthreads();
       vec_task<0>(vec_of(B3[mi], 1.0 / (double)p, (double)(p + 1)));
-      // column pos of F = c X and the residual F^p s_pos - e_pos = u - e_pos
+      // column pos of the result (lambda_bar^(-1/p) X e_pos, or lambda_bar^(1/p) X^(p-1)
+      // M_0 e_pos for A^(1/p)) and the residual F^p s_pos - e_pos = u - e_pos of
+      // F = lambda_bar^(-1/p) X
       float r = 0.f;
       for (int i = tid; i < m; i += blockDim.x) {
-        y_s[i] = c * yg[i];
+        y_s[i] = c_out * yg[i];
         const float d = ug[i] - (i == pos ? 1.f : 0.f);
         r += d * d;
       }
@@ -1087,6 +1097,10 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
       SliceLoad xl{X[xc].q, plane, LD, ldexp(1.0, X[xc].e - 7)};
       const float xs = ldexpf(1.f, X[xc].e - 7);
       resid = refine_column(xl, c, S, m, pos, p, a.refine_steps, y_s, v_s, w_s, red_s);
+      if (a.sign > 0) {          // A^(1/1): column pos of S itself (the iteration still checks S)
+        for (int i = tid; i < m; i += blockDim.x) y_s[i] = S[pos * m + i];
+        __syncthreads();
+      }
       // condition estimate lambda_bar / lambda_min = lambda_max(X) (X ~ (S/lambda_bar)^(-1))
       kest = power_max_slices(X[xc].q, plane, LD, xs, m, mp, reinterpret_cast<float*>(v_s),
                               reinterpret_cast<float*>(w_s), reinterpret_cast<float*>(red_s), 6);

@@ -43,6 +43,7 @@ def test_status_strings_and_defaults(lib):
     o = pkg.Opts()
     lib.submat_default_opts(ctypes.byref(o))
     assert o.precision == pkg.PREC_MIXED_F16 and o.k_max == 40 and o.use_graph == 1
+    assert o.root_sign == -1 and o.kappa_max == 100.0
 
 
 def _plan_status(lib, rowptr, colind, p=2):
@@ -56,6 +57,7 @@ def _plan_status(lib, rowptr, colind, p=2):
 
 
 def test_host_side_validation(lib):
+    import paper_1710_10899_gb300 as pkg
     # these are rejected before the library touches the GPU
     assert _plan_status(lib, [0, 1], [0], p=0) == "SUBMAT_EINVAL"
     assert _plan_status(lib, [1, 1], [0]) == "SUBMAT_EINVAL"            # rowptr[0] != 0
@@ -64,6 +66,15 @@ def test_host_side_validation(lib):
     big = 1537
     assert _plan_status(lib, [0, big], np.arange(big)) == "SUBMAT_ETOOBIG"
     assert lib.submat_plan(None, 2, None, None) != 0
+    # root_sign other than -1 / +1
+    o = pkg.Opts()
+    lib.submat_default_opts(ctypes.byref(o))
+    o.root_sign = 0
+    rp = np.array([0, 1], dtype=np.int32)
+    ci = np.array([0], dtype=np.int32)
+    csr = pkg.CSR(1, 1, rp.ctypes.data, ci.ctypes.data, 0)
+    h = ctypes.c_void_p()
+    assert pkg.STATUS[lib.submat_plan(ctypes.byref(csr), 2, ctypes.byref(o), ctypes.byref(h))] == "SUBMAT_EINVAL"
 
 
 def test_noalloc_host_side_validation(lib):

@@ -32,6 +32,18 @@ def test_grad_matches_oracle(sm, p):
     assert np.abs(g - gref).max() <= 1e-10 * np.abs(gref).max()
 
 
+@pytest.mark.parametrize("p", [2, 3])
+def test_positive_root_grad_matches_oracle(sm, p):
+    a = wl.overlap_uniform(n=400, kappa=1e3)
+    w = wl.random_on_pattern(a, seed=2)
+    plan = sm.submat_plan(a.rowptr, a.colind, p, root_sign=1)
+    v = torch.tensor(a.vals, device="cuda")
+    sm.submat_invroot(plan, v)
+    g = sm.submat_invroot_backward(plan, torch.tensor(w, device="cuda")).cpu().numpy()
+    gref = oracle.grad(a.rowptr, a.colind, a.vals, p, w, sign=1)
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) <= 1e-10
+
+
 def test_autograd_and_central_differences(sm):
     a = wl.overlap_grad(n=2048)                 # the differentiation workload, scaled down
     w = torch.tensor(wl.random_on_pattern(a, seed=1), device="cuda")

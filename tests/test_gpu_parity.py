@@ -295,3 +295,39 @@ def test_tcgen05_and_mma_sync_engines_agree(sm, p):
         assert row_errors(a, y, ref, rows).max() <= TOL["mixed"]
         outs[prec] = y
     assert row_errors(a, outs["mixed"], outs["mixed_sync"], range(a.n)).max() <= 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Positive p-th roots (Sec. 4.2; root_sign = +1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_positive_root_small_all_rows(sm, precision):
+    a = wl.overlap_small()
+    plan, y = run(sm, a, 2, precision, root_sign=1)
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, 2, sign=1)
+    assert row_errors(a, y, ref, range(a.n)).max() <= TOL[precision]
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_positive_root_uniform_sampled(sm, p, precision):
+    a = wl.overlap_uniform(n=4096)
+    plan, y = run(sm, a, p, precision, root_sign=1)
+    rows = sample_rows(a, 100, seed=10 + p)
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, p, rows=rows, sign=1)
+    assert row_errors(a, y, ref, rows).max() <= TOL[precision]
+    assert plan.report()["n_fallback"] == 0
+
+
+def test_positive_root_dense_pattern_is_full_root(sm):
+    import scipy.linalg as sl
+    rng = np.random.default_rng(19)
+    b = rng.standard_normal((90, 90))
+    dense = b @ b.T / 90 + 0.3 * np.eye(90)
+    a = wl.dense_to_csr(dense, keep=np.ones((90, 90), dtype=bool))
+    for p in (2, 3):
+        plan, y = run(sm, a, p, "mixed", root_sign=1)
+        full = np.real(sl.fractional_matrix_power(dense, 1.0 / p))
+        yd = oracle.to_dense(a.n, a.rowptr, a.colind, y)
+        assert np.abs(yd - full.T).max() / np.abs(full).max() < 1e-6
