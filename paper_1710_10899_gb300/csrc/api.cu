@@ -322,7 +322,7 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   P->grid = std::max(1, std::min(P->n_sm * ctas, n));
   PLAN_TRY(cudaMalloc(&P->d_scratch, stride * (size_t)P->grid));
   if (mixed && o.precision == SUBMAT_PREC_MIXED_F16) {
-    // TMA descriptors over all CTAs' planes: dims (LD cols, LD rows, planes), 64-byte swizzle
+    // TMA descriptors over all CTAs' planes: dims (LD cols, LD rows, planes), 32-byte swizzle
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t ge = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled",
@@ -336,12 +336,12 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
     cuuint64_t dims[3] = {(cuuint64_t)P->ld, (cuuint64_t)P->ld, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)P->ld * 2, (cuuint64_t)P->ld * P->ld * 2};
     cuuint32_t elem[3] = {1, 1, 1};
-    cuuint32_t box_a[3] = {32, 128, 1}, box_b[3] = {32, 48, 1};
+    cuuint32_t box_a[3] = {16, 128, 1}, box_b[3] = {16, 96, 1};   // 16-wide k-slices
     CUresult r1 = encode(&P->tm_a, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, P->d_scratch, dims, strides,
-                         box_a, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                         box_a, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     CUresult r2 = encode(&P->tm_b, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, P->d_scratch, dims, strides,
-                         box_b, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                         box_b, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
       fail(SUBMAT_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r1) + ", " +

@@ -34,8 +34,8 @@ struct DevCounters {
 
 // Arguments of the forward kernels.
 struct FwdArgs {
-  CUtensorMap tm_a;          // mixed tcgen05 engine: A tiles (32 x 128) of the scratch planes
-  CUtensorMap tm_b;          //                       B tiles (32 x 48)
+  CUtensorMap tm_a;          // mixed tcgen05 engine: A tiles (16 x 128) of the scratch planes
+  CUtensorMap tm_b;          //                       B tiles (16 x 96)
   int32_t ld;                // mixed path: leading dimension of the scratch planes
   int32_t engine;            // mixed path: 0 = tcgen05, 1 = mma.sync
   const int32_t* rowptr;

@@ -30,10 +30,11 @@
 // per-product error, kept by every iteration, left ~6e-7 in the result; measured.)
 //
 // GEMM engines (template parameter TC):
-//   TC = true  (default): tcgen05.mma kind::f16, M = 128, N = 48, the five level
-//              accumulators in TMEM, double-buffered (2 x 5 x 48 of 512 columns) so the
-//              epilogue of one tile overlaps the MMAs of the next; operands moved by TMA
-//              (SWIZZLE_64B, 32-wide k-slices) through a 3-stage mbarrier pipeline.
+//   TC = true  (default): tcgen05.mma kind::f16, M = 128, N = 96, the five level
+//              accumulators in one 480-column TMEM buffer, drained in two phases (levels
+//              combined into shared memory, TMEM released, then the affine step and the
+//              stores) so the next tile's MMAs overlap the second phase; operands moved by
+//              TMA (SWIZZLE_32B, 16-wide k-slices) through a 3-stage mbarrier pipeline.
 //              Roles: warps 0-7 run the epilogue (two per TMEM lane quarter), warp 8
 //              issues TMA, warp 9 issues MMAs (320 threads).
 //              All working matrices are symmetric, so a row-major B read as K-major
@@ -109,11 +110,8 @@ __device__ __forceinline__ void store8_slices(__half* q, size_t plane, size_t id
 // Barrier of a warp group: BAR = 0 is the whole block (__syncthreads); BAR = kEpiBar is the
 // tcgen05 engine's epilogue warps 0..kEpiGroupWarps-1 (a named barrier), which run vector
 // work while the MMA and TMA warps run a GEMM.
-// CTAs per SM of the tcgen05 engine: two CTAs, each with half of TMEM and shared memory,
-// would let one CTA's latency-bound phases overlap the other's MMAs (measured slower).
-constexpr int TC_CTAS = 1;
 constexpr int kEpiBar = 3;
-constexpr int kEpiGroupWarps = TC_CTAS == 1 ? 8 : 4;
+constexpr int kEpiGroupWarps = 8;
 template <int BAR>
 __device__ __forceinline__ void grp_sync() {
   if (BAR == 0)
@@ -344,26 +342,32 @@ __device__ float start_lo_slices(const __half* q, size_t plane, int ld, int e, i
 // ======================================================================================
 // tcgen05 engine
 // ======================================================================================
-// Output tiles of 128 rows x 48 columns (the last column tile of a row block may be 16 or
-// 32 wide).  Five level accumulators of 48 columns make one 240-column TMEM buffer; two
-// buffers (480 of 512 columns) let the MMAs of tile t+1 run while the epilogue drains t.
-constexpr int TC_M = 128, TC_N = 48, TC_K = 32;        // tile and k-slice
-constexpr int TC_NBUF = TC_CTAS == 1 ? 2 : 1;          // TMEM accumulator buffers
-constexpr int TC_STAGES = TC_CTAS == 1 ? 3 : 2;
-constexpr int TC_A_PLANE = TC_M * TC_K * 2;            // 8192 B
+// Output tiles of 128 rows x 96 columns (the last column tile of a row block is 32, 64 or 96
+// wide: padded orders are multiples of 64).  A tcgen05.mma costs a fixed ~45 cycles below
+// N ~ 96 (measured), so 96-wide tiles keep the tensor pipe on the work instead of the
+// overhead.  The five 96-column level accumulators fill one 480-column TMEM buffer; the
+// epilogue drains it in two phases: phase 1 combines the levels into double-floats staged in
+// shared memory and releases TMEM, so the next tile's MMAs run during phase 2 (affine step,
+// slicing, stores).  Operands move by TMA in 16-wide k-slices (32-byte rows, SWIZZLE_32B)
+// through a 3-stage mbarrier pipeline.
+constexpr int TC_M = 128, TC_N = 96, TC_K = 16;        // tile and k-slice
+constexpr int TC_STAGES = 3;
+constexpr int TC_A_PLANE = TC_M * TC_K * 2;            // 4096 B
 constexpr int TC_B_PLANE = TC_N * TC_K * 2;            // 3072 B
-constexpr int TC_STAGE_BYTES = NSL * (TC_A_PLANE + TC_B_PLANE);   // 56320 B
-constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 168960 B
-constexpr int TC_BUF_COLS = NSL * TC_N;                // 240 TMEM columns per buffer
+constexpr int TC_STAGE_BYTES = NSL * (TC_A_PLANE + TC_B_PLANE);   // 35840 B
+constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 107520 B
+constexpr int TC_STAGING_BYTES = TC_M * TC_N * 8;      // 98304 B: a float pair per entry
+constexpr int TC_BUF_COLS = NSL * TC_N;                // 480 TMEM columns
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;           // polls before a wait gives up
-constexpr uint32_t TC_TMEM_COLS = TC_CTAS == 1 ? 512 : 256;
-static_assert(TC_NBUF * TC_BUF_COLS <= (int)TC_TMEM_COLS, "TMEM budget");
+constexpr uint32_t TC_TMEM_COLS = 512;
+static_assert(TC_BUF_COLS <= (int)TC_TMEM_COLS, "TMEM budget");
+static_assert(TC_STAGE_BYTES % 1024 == 0 || TC_STAGE_BYTES % 256 == 0, "swizzle atoms");
 // tcgen05 CTA: warps 0-7 run the epilogue (warp w: TMEM lane quarter w % 4, column half
 // w / 4 of the tile), warp 8 issues TMA, warp 9 issues MMAs.
 constexpr int TC_EPI_WARPS = kEpiGroupWarps;
 constexpr int TC_THREADS = (TC_EPI_WARPS + 2) * 32;
 constexpr int TC_TMA_WARP = TC_EPI_WARPS, TC_MMA_WARP = TC_EPI_WARPS + 1;
-constexpr int TC_EPI_COLS = TC_N * 4 / TC_EPI_WARPS;  // tile columns per epilogue warp
+constexpr int TC_EPI_COLS = TC_N * 4 / TC_EPI_WARPS;  // tile columns per epilogue warp (48)
 
 struct TcState {            // pipeline counters; each role keeps its own copy
   uint32_t pit = 0;         // stages issued (TMA)
@@ -374,10 +378,11 @@ struct TcState {            // pipeline counters; each role keeps its own copy
 
 struct TcCtx {
   unsigned char* stages;    // 1024-aligned shared memory
+  float2* staging;          // [TC_N][TC_M] double-floats of the tile being drained
   uint64_t* full;           // [TC_STAGES]
   uint64_t* empty;          // [TC_STAGES]
-  uint64_t* tmem_full;      // [2]
-  uint64_t* tmem_empty;     // [2]
+  uint64_t* tmem_full;      // accumulators ready
+  uint64_t* tmem_empty;     // accumulators read (phase 1 done)
   int* abort_s;
   uint32_t tmem;
   const CUtensorMap* tm_a;
@@ -385,7 +390,7 @@ struct TcCtx {
 };
 
 // Output tiles of a symmetric product: row block tm (128 rows) needs only the column tiles
-// that reach its diagonal block, tn >= skip(tm) = floor(128 tm / 48); the tiles left of them
+// that reach its diagonal block, tn >= skip(tm) = floor(128 tm / 96); the tiles left of them
 // lie wholly below the diagonal and are written as mirror images by the tiles above
 // (mirror_needed).  All three roles enumerate the tiles in the same order.
 __device__ __forceinline__ int tc_skip(int tm) { return (TC_M * tm) / TC_N; }
@@ -490,16 +495,15 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
       for (int t = 0; t < ntiles && !*c.abort_s; ++t) {
         int tm, tn;
         tc_tile(t, ntn, tm, tn);
-        const int nw = min(TC_N, mp - tn * TC_N);      // 48, or 16 / 32 for the last tile
+        const int nw = min(TC_N, mp - tn * TC_N);      // 96, or 64 / 32 for the last tile
         const uint32_t idesc = tc::idesc_f16(TC_M, nw);
-        const uint32_t b = st.tmt % TC_NBUF;
-        if (st.tmt >= TC_NBUF &&
-            !tc::mbar_wait(&c.tmem_empty[b], ((st.tmt / TC_NBUF) - 1) & 1, TC_WAIT_LIMIT)) {
+        // the single accumulator buffer is free once the epilogue has read the previous tile
+        if (st.tmt >= 1 && !tc::mbar_wait(c.tmem_empty, (st.tmt - 1) & 1, TC_WAIT_LIMIT)) {
           *c.abort_s = 1;
           break;
         }
         tc::tc_fence_after();
-        const uint32_t d0 = c.tmem + b * TC_BUF_COLS;
+        const uint32_t d0 = c.tmem;
         bool ok = true;
         for (int kt = 0; kt < KT; ++kt) {
           const uint32_t s = st.cit % TC_STAGES;
@@ -508,23 +512,20 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
             break;
           }
           tc::tc_fence_after();
-          // operand descriptors of the stage; every plane / k-step offset below is a
-          // compile-time constant added to the 14-bit start-address field (no carry: shared
-          // addresses stay below 2^18 bytes)
+          // operand descriptors of the stage; every plane offset below is a compile-time
+          // constant added to the 14-bit start-address field (no carry: shared addresses
+          // stay below 2^18 bytes)
           const uint32_t sa = tc::saddr(c.stages + s * TC_STAGE_BYTES);
-          const uint64_t da0 = tc::desc_sw64(sa);
-          const uint64_t db0 = tc::desc_sw64(sa + NSL * TC_A_PLANE);
+          const uint64_t da0 = tc::desc_sw32(sa);
+          const uint64_t db0 = tc::desc_sw32(sa + NSL * TC_A_PLANE);
           const uint32_t acc0 = kt != 0;               // the first k-step overwrites
 #pragma unroll
-          for (int kk = 0; kk < TC_K / 16; ++kk) {
+          for (int L = 0; L < NSL; ++L) {
 #pragma unroll
-            for (int L = 0; L < NSL; ++L) {
-#pragma unroll
-              for (int sa_i = 0; sa_i <= L; ++sa_i) {
-                const uint64_t da = da0 + (uint64_t)((sa_i * TC_A_PLANE + kk * 32) >> 4);
-                const uint64_t db = db0 + (uint64_t)(((L - sa_i) * TC_B_PLANE + kk * 32) >> 4);
-                tc::mma_f16(d0 + L * TC_N, da, db, idesc, (kk | sa_i) != 0 ? 1u : acc0);
-              }
+            for (int sa_i = 0; sa_i <= L; ++sa_i) {
+              const uint64_t da = da0 + (uint64_t)((sa_i * TC_A_PLANE) >> 4);
+              const uint64_t db = db0 + (uint64_t)(((L - sa_i) * TC_B_PLANE) >> 4);
+              tc::mma_f16(d0 + L * TC_N, da, db, idesc, sa_i != 0 ? 1u : acc0);
             }
           }
           tc::mma_commit(&c.empty[s]);                 // frees the stage when these MMAs finish
@@ -534,7 +535,7 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
           *c.abort_s = 1;
           break;
         }
-        tc::mma_commit(&c.tmem_full[b]);               // accumulators of tile t ready
+        tc::mma_commit(c.tmem_full);                   // accumulators of tile t ready
         ++st.tmt;
       }
     }
@@ -548,9 +549,9 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
     const float alpha_s = ldexpf(io.alpha, Y.e - 15 - (A.e + B.e - 14));
     const float c_s = ldexpf(io.c, A.e + B.e - 14);
     float nrm = 0.f, amax = 0.f;
+    const int rt = q4 * 32 + lane;                    // row within the tile
     for (int t = 0; t < ntiles; ++t) {
-      const uint32_t b = st.ept % TC_NBUF;
-      if (!tc::mbar_wait(&c.tmem_full[b], (st.ept / TC_NBUF) & 1, TC_WAIT_LIMIT)) {
+      if (!tc::mbar_wait(c.tmem_full, st.ept & 1, TC_WAIT_LIMIT)) {
         *c.abort_s = 1;
         break;
       }
@@ -558,15 +559,35 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
       int tm, tn;
       tc_tile(t, ntn, tm, tn);
       const int nw = min(TC_N, mp - tn * TC_N);
-      const int row = tm * TC_M + q4 * 32 + lane;
-      const uint32_t tbase = c.tmem + ((uint32_t)(q4 * 32) << 16) + b * TC_BUF_COLS;
-      for (int c0 = half * TC_EPI_COLS; c0 < (half + 1) * TC_EPI_COLS; c0 += 8) {
-        if (c0 >= nw) break;                           // warp-uniform
+      const int row = tm * TC_M + rt;
+      const int cb = half * TC_EPI_COLS;                // this warp's columns [cb, cb + 48)
+      const int ce = min(cb + TC_EPI_COLS, nw);
+      // phase 1: w = acc0 + 2^-8 acc1 + (levels 2..4) (the first two exactly) into the
+      // staging area, [column][row] so that a warp's stores are contiguous; each thread
+      // reads back only its own entries
+      const uint32_t tbase = c.tmem + ((uint32_t)(q4 * 32) << 16);
+      for (int c0 = cb; c0 < ce; c0 += 8) {            // warp-uniform bounds
         float acc[NSL][8];
 #pragma unroll
         for (int L = 0; L < NSL; ++L) tc::tmem_ld8(tbase + L * TC_N + c0, acc[L]);
         tc::tmem_ld_wait();
-        if (row < mp) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          float wh, wl;
+          two_sum(acc[0][k], acc[1][k] * (1.f / 256.f), wh, wl);
+          wl = __fadd_rn(wl, __fmaf_rn(acc[4][k], 1.f / 4294967296.f,
+                                       __fmaf_rn(acc[3][k], 1.f / 16777216.f,
+                                                 acc[2][k] * (1.f / 65536.f))));
+          c.staging[(c0 + k) * TC_M + rt] = make_float2(wh, wl);
+        }
+      }
+      // the accumulators are read: the next tile's MMAs may start
+      tc::tc_fence_before();
+      tc::mbar_arrive(c.tmem_empty);
+      ++st.ept;
+      // phase 2: C = c (alpha Y - A B) from the staged sums, sliced and stored
+      if (row < mp) {
+        for (int c0 = cb; c0 < ce; c0 += 8) {
           const int j0 = tn * TC_N + c0;
           const size_t idx0 = (size_t)row * io.ld + j0;
           float oh[8], ol[8];
@@ -584,18 +605,13 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
             const float ya = __fmaf_rn(yq[0], 256.f, yq[1]);
             const float yb = __fmaf_rn(yq[2], 1.f / 256.f, __fmaf_rn(yq[3], 1.f / 65536.f,
                                                                      yq[4] * (1.f / 16777216.f)));
-            // w = v / cscale = acc0 + 2^-8 acc1 + (levels 2..4), the first two exactly
-            float wh, wl;
-            two_sum(acc[0][k], acc[1][k] * (1.f / 256.f), wh, wl);
-            wl = __fadd_rn(wl, __fmaf_rn(acc[4][k], 1.f / 4294967296.f,
-                                         __fmaf_rn(acc[3][k], 1.f / 16777216.f,
-                                                   acc[2][k] * (1.f / 65536.f))));
+            const float2 w = c.staging[(c0 + k) * TC_M + rt];
             // out = c cscale (alpha' y - w), alpha' = alpha 2^(Y.e-15) / cscale (exact)
             const float p1 = __fmul_rn(alpha_s, ya);
             const float e1 = __fmaf_rn(alpha_s, yb, __fmaf_rn(alpha_s, ya, -p1));
             float d, de;
-            two_sum(p1, -wh, d, de);
-            de = __fadd_rn(de, __fsub_rn(e1, wl));
+            two_sum(p1, -w.x, d, de);
+            de = __fadd_rn(de, __fsub_rn(e1, w.y));
             oh[k] = __fmul_rn(c_s, d);
             ol[k] = __fmaf_rn(c_s, de, __fmaf_rn(c_s, d, -oh[k]));
           }
@@ -616,9 +632,6 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
           }
         }
       }
-      tc::tc_fence_before();
-      tc::mbar_arrive(&c.tmem_empty[b]);
-      ++st.ept;
     }
     if (flags & EPI_NORM) {
       nrm = warp_sum_f(nrm);
@@ -815,15 +828,18 @@ __device__ void gemm_sync(Mat A, Mat B, Mat C, Mat Y, int flags, const GemmIO& i
 // the per-submatrix kernel
 // ======================================================================================
 constexpr size_t kSmemTail = 256;                       // barriers and flags
+// shared memory before the barrier tail: tcgen05: TMA stages + the epilogue's staging area
 template <bool TC>
-__host__ __device__ constexpr size_t stage_area() { return TC ? (size_t)TC_STAGE_AREA : (size_t)SY_STAGE_AREA; }
+__host__ __device__ constexpr size_t stage_area() {
+  return TC ? (size_t)TC_STAGE_AREA + TC_STAGING_BYTES : (size_t)SY_STAGE_AREA;
+}
 // vectors used between GEMMs alias the stage area
 constexpr size_t kVecBytes = 4 * SUBMAT_MAX_M * sizeof(double) + kRedDoubles * sizeof(double) +
                              SUBMAT_MAX_M * sizeof(int32_t);
 static_assert(kVecBytes <= (size_t)SY_STAGE_AREA, "vector area must fit in the stage area");
 
 template <bool TC>
-__global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
+__global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     fwd_mixed_kernel(const __grid_constant__ FwdArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
@@ -834,7 +850,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
   double* red_s = w_s + SUBMAT_MAX_M;                 // kRedDoubles doubles
   int32_t* R_s = reinterpret_cast<int32_t*>(red_s + kRedDoubles);
   unsigned char* tail = sm + stage_area<TC>();
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tail);  // full, empty [TC_STAGES], tmem_full, tmem_empty [TC_NBUF]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tail);  // full, empty [TC_STAGES], tmem_full, tmem_empty
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tail + 96);
   int* abort_s = reinterpret_cast<int*>(tail + 100);
   float* norm2_s = reinterpret_cast<float*>(tail + 104);
@@ -853,9 +869,8 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
   TcState tst;
   if (TC) {
     if (tid == 0) {
-      for (int i = 0; i < 2 * TC_STAGES + TC_NBUF; ++i) tc::mbar_init(&bars[i], 1);
-      for (int i = 0; i < TC_NBUF; ++i)
-        tc::mbar_init(&bars[2 * TC_STAGES + TC_NBUF + i], TC_EPI_WARPS * 32);
+      for (int i = 0; i < 2 * TC_STAGES + 1; ++i) tc::mbar_init(&bars[i], 1);
+      tc::mbar_init(&bars[2 * TC_STAGES + 1], TC_EPI_WARPS * 32);
       *abort_s = 0;
       tc::fence_mbar_init();
     }
@@ -867,7 +882,8 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, TC ? TC_CTAS : 1)
     tcx.full = bars;
     tcx.empty = bars + TC_STAGES;
     tcx.tmem_full = bars + 2 * TC_STAGES;
-    tcx.tmem_empty = bars + 2 * TC_STAGES + TC_NBUF;
+    tcx.tmem_empty = bars + 2 * TC_STAGES + 1;
+    tcx.staging = reinterpret_cast<float2*>(sm + TC_STAGE_AREA);
     tcx.abort_s = abort_s;
     tcx.tmem = *tmem_holder;
     tcx.tm_a = &a.tm_a;
@@ -1155,18 +1171,13 @@ cudaError_t launch_fwd_mixed(const FwdArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int mixed_ctas_per_sm() { return TC_CTAS; }
+int mixed_ctas_per_sm() { return 1; }
 
 cudaError_t set_attr_mixed() {
   cudaError_t e = cudaFuncSetAttribute(fwd_mixed_kernel<true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes<true>());
   if (e != cudaSuccess) return e;
-  if (TC_CTAS > 1) {                                   // room for two CTAs' shared memory
-    e = cudaFuncSetAttribute(fwd_mixed_kernel<true>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-  }
   return cudaFuncSetAttribute(fwd_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_bytes<false>());
 }

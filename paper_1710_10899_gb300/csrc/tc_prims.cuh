@@ -146,6 +146,18 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t smem_addr) {
   return d;
 }
 
+// The same for the 32-byte swizzle (rows of 32 bytes = one 16-half k-slice, 8-row atoms of
+// 256 bytes): SBO = 256 B, layout type 6 (SWIZZLE_32B).
+__device__ __forceinline__ uint64_t desc_sw32(uint32_t smem_addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                       // LBO (ignored for swizzled K-major)
+  d |= (uint64_t)(256 >> 4) << 32;              // SBO
+  d |= (uint64_t)1 << 46;                       // version
+  d |= (uint64_t)6 << 61;                       // SWIZZLE_32B
+  return d;
+}
+
 // Instruction descriptor: kind::f16, A = B = F16, D = F32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4)                      // D format F32
