@@ -74,9 +74,16 @@ static __device__ void gemm64(const double* __restrict__ A, const double* __rest
         }
       }
   }
-  if (epi == EPI_M) {
+  if (epi == EPI_M) {          // added in warp order: the result does not depend on timing
     nrm = warp_sum(nrm);
-    if ((tid & 31) == 0) atomicAdd(norm2_s, nrm);
+    __syncthreads();           // the tile buffers are no longer read
+    if ((tid & 31) == 0) smem[tid >> 5] = nrm;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nwarps(); ++w) t += smem[w];
+      *norm2_s += t;
+    }
   }
   __syncthreads();
 }

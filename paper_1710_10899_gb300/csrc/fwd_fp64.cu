@@ -46,8 +46,6 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_fp64_kernel(FwdArgs a) {
 
     const double lam = gather_submatrix(a.rowptr, a.colind, a.vals_in, j, m, R_s, S, red_s);
     const double inv_lam = 1.0 / lam;
-    if (tid == 0) *norm2_s = 0.0;
-    __syncthreads();
     double nrm = 0.0;
     for (size_t e = tid; e < mat; e += blockDim.x) {
       const int i = (int)(e / mp), jj = (int)(e % mp);
@@ -60,9 +58,10 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_fp64_kernel(FwdArgs a) {
       B3[0][e] = mv;
     }
     nrm = warp_sum(nrm);
-    if ((tid & 31) == 0) atomicAdd(norm2_s, nrm);
+    if ((tid & 31) == 0) red_s[tid >> 5] = nrm;
     __syncthreads();
-    double nrm2 = *norm2_s;
+    double nrm2 = 0.0;
+    for (int w = 0; w < nwarps(); ++w) nrm2 += red_s[w];     // in warp order
     float lo = 0.5f * start_lo(S, m, inv_lam, v_s, w_s, red_s, kStartLoSteps);
 
     // tracked vectors (p >= 2): y = X_k e_pos (A^(-1/p)) or X_k^(p-1) M_0 e_pos (A^(1/p)) in

@@ -77,7 +77,7 @@ struct Mat {
 struct GemmIO {     // what every GEMM call shares within one submatrix
   int mp, m, p, ld;
   size_t plane;     // ld * ld
-  float* norm2_s;
+  float* norm_part;  // ||.||_F^2 partial sums, one slot per writing warp (summed in order)
   unsigned* amax_s;
   float c, alpha;          // C = c (alpha Y - A B)
 };
@@ -118,6 +118,24 @@ __device__ __forceinline__ void grp_sync() {
     __syncthreads();
   else
     asm volatile("bar.sync %0, %1;\n" ::"n"(BAR), "n"(kEpiGroupWarps * 32) : "memory");
+}
+// Barrier of the epilogue warps that also returns whether any of them passed true.
+__device__ __forceinline__ bool epi_sync_any(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+      " bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kEpiBar), "n"(kEpiGroupWarps * 32)
+      : "memory");
+  return r != 0;
+}
+// Sum of per-warp partial sums in warp order, so the result does not depend on timing (the
+// norm steers the step constants and the stopping test).
+__device__ __forceinline__ float sum_parts(const float* part, int n) {
+  float r = 0.f;
+  for (int w = 0; w < n; ++w) r += part[w];
+  return r;
 }
 template <int BAR>
 __device__ __forceinline__ int grp_warps() { return BAR == 0 ? nwarps() : kEpiGroupWarps; }
@@ -346,17 +364,29 @@ __device__ float start_lo_slices(const __half* q, size_t plane, int ld, int e, i
 // wide: padded orders are multiples of 64).  A tcgen05.mma costs a fixed ~45 cycles below
 // N ~ 96 (measured), so 96-wide tiles keep the tensor pipe on the work instead of the
 // overhead.  The five 96-column level accumulators fill one 480-column TMEM buffer; the
-// epilogue drains it in two phases: phase 1 combines the levels into double-floats staged in
-// shared memory and releases TMEM, so the next tile's MMAs run during phase 2 (affine step,
-// slicing, stores).  Operands move by TMA in 16-wide k-slices (32-byte rows, SWIZZLE_32B)
-// through a 3-stage mbarrier pipeline.
+// epilogue drains it in phases: phase 1 (a thread per TMEM lane, i.e. per tile row)
+// combines the levels into double-floats staged in shared memory and releases TMEM, so the
+// next tile's MMAs run during the rest; phase 2 (the affine step, slicing and stores) maps
+// consecutive threads to consecutive 8-column chunks of a row, so a warp's global loads and
+// stores cover whole row segments instead of 32 rows; phase 3 writes the mirror images of
+// the entries that fall in skipped tiles (see tc_skip) from the slices left in shared
+// memory, a thread per tile row, so that those stores are contiguous too.  Operands move by
+// TMA in 16-wide k-slices (32-byte rows, SWIZZLE_32B) through a 2-stage mbarrier pipeline
+// (a third stage measured no faster, and the staging area needs the room).
 constexpr int TC_M = 128, TC_N = 96, TC_K = 16;        // tile and k-slice
-constexpr int TC_STAGES = 3;
+constexpr int TC_STAGES = 2;
 constexpr int TC_A_PLANE = TC_M * TC_K * 2;            // 4096 B
 constexpr int TC_B_PLANE = TC_N * TC_K * 2;            // 3072 B
 constexpr int TC_STAGE_BYTES = NSL * (TC_A_PLANE + TC_B_PLANE);   // 35840 B
-constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 107520 B
-constexpr int TC_STAGING_BYTES = TC_M * TC_N * 8;      // 98304 B: a float pair per entry
+constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 71680 B
+// Staging area: per tile row, NSL x TC_CH 16-byte units (unit (k, ch) of row r holds the
+// double-floats of entries (r, 8 ch + 2k), (r, 8 ch + 2k + 1) for k < 4 after phase 1, and
+// plane k of entries (r, 8 ch .. 8 ch + 7) after phase 2), plus one unit of padding: the odd
+// row stride makes a thread-per-row access (phases 1 and 3) and a thread-per-chunk access
+// (phase 2) both free of bank conflicts.
+constexpr int TC_CH = TC_N / 8;                        // 8-column chunks per tile row (12)
+constexpr int TC_SROW = NSL * TC_CH + 1;               // units per staged row (61)
+constexpr int TC_STAGING_BYTES = TC_M * TC_SROW * 16;  // 124928 B
 constexpr int TC_BUF_COLS = NSL * TC_N;                // 480 TMEM columns
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;           // polls before a wait gives up
 constexpr uint32_t TC_TMEM_COLS = 512;
@@ -378,7 +408,7 @@ struct TcState {            // pipeline counters; each role keeps its own copy
 
 struct TcCtx {
   unsigned char* stages;    // 1024-aligned shared memory
-  float2* staging;          // [TC_N][TC_M] double-floats of the tile being drained
+  uint4* staging;           // [TC_M][TC_SROW] units of the tile being drained
   uint64_t* full;           // [TC_STAGES]
   uint64_t* empty;          // [TC_STAGES]
   uint64_t* tmem_full;      // accumulators ready
@@ -416,13 +446,11 @@ __device__ __forceinline__ bool mirror_needed(int i, int j, int tm) {
   return tmj > tm && (i / TC_N) < tc_skip(tmj);
 }
 
-// Planes of the eight entries (row, j0..j0+7) of a symmetric product: one 16-byte store per
-// plane, and each entry whose mirror lies in a skipped tile also at (j, row) (a warp's 32
-// consecutive rows make these 64-byte contiguous stores).  Returns the mask of mirrored
-// entries.
-__device__ __forceinline__ unsigned store8_sym(__half* q, size_t plane, int ld, int row,
-                                               int j0, int tm, const float* vh, const float* vl,
-                                               int e) {
+// Planes of the eight entries (row, j0..j0+7): one 16-byte store per plane to C, and the
+// same planes to the staging units su[0], su[TC_CH], ... when keep (for the mirror pass).
+__device__ __forceinline__ void store8_planes(__half* q, size_t plane, int ld, int row, int j0,
+                                              const float* vh, const float* vl, int e,
+                                              uint4* su, bool keep) {
   __align__(16) __half out[NSL][8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -433,22 +461,11 @@ __device__ __forceinline__ unsigned store8_sym(__half* q, size_t plane, int ld, 
   }
   const size_t idx0 = (size_t)row * ld + j0;
 #pragma unroll
-  for (int k = 0; k < NSL; ++k)
-    *reinterpret_cast<uint4*>(q + k * plane + idx0) = *reinterpret_cast<const uint4*>(out[k]);
-  unsigned mask = 0u;
-  if (mirror_needed(row, j0 + 7, tm)) {             // the chunk reaches a later row block
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int j = j0 + c;
-      if (mirror_needed(row, j, tm)) {
-        mask |= 1u << c;
-        const size_t m_idx = (size_t)j * ld + row;
-#pragma unroll
-        for (int k = 0; k < NSL; ++k) q[k * plane + m_idx] = out[k][c];
-      }
-    }
+  for (int k = 0; k < NSL; ++k) {
+    const uint4 v = *reinterpret_cast<const uint4*>(out[k]);
+    *reinterpret_cast<uint4*>(q + k * plane + idx0) = v;
+    if (keep) su[k * TC_CH] = v;
   }
-  return mask;
 }
 
 // C = A B^T on the tcgen05 engine (see the header comment).  All TC_THREADS threads call it.
@@ -544,14 +561,17 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
     // meanwhile
     if (vt) vec_task<kEpiBar>(*vt);
     const int q4 = warp & 3, half = warp >> 2;
+    const int etid = tid;                              // 0 .. 255 (warps 0..7)
     // the level sums count in units of cscale = 2^(A.e + B.e - 14), Y's planes in units of
     // 2^(Y.e - 15)
     const float alpha_s = ldexpf(io.alpha, Y.e - 15 - (A.e + B.e - 14));
     const float c_s = ldexpf(io.c, A.e + B.e - 14);
     float nrm = 0.f, amax = 0.f;
-    const int rt = q4 * 32 + lane;                    // row within the tile
+    const int rt = q4 * 32 + lane;                    // phase 1: this thread's tile row
     for (int t = 0; t < ntiles; ++t) {
-      if (!tc::mbar_wait(c.tmem_full, st.ept & 1, TC_WAIT_LIMIT)) {
+      // the epilogue warps meet at barriers below, so they leave together
+      const bool timed_out = !tc::mbar_wait(c.tmem_full, st.ept & 1, TC_WAIT_LIMIT);
+      if (epi_sync_any(timed_out)) {
         *c.abort_s = 1;
         break;
       }
@@ -559,83 +579,135 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
       int tm, tn;
       tc_tile(t, ntn, tm, tn);
       const int nw = min(TC_N, mp - tn * TC_N);
-      const int row = tm * TC_M + rt;
-      const int cb = half * TC_EPI_COLS;                // this warp's columns [cb, cb + 48)
-      const int ce = min(cb + TC_EPI_COLS, nw);
+      const int nch = nw / 8;
+      // tile-uniform: do any of its columns reach a later row block (mirror images)?
+      const bool tile_mirror = (tn * TC_N + nw - 1) / TC_M > tm;
       // phase 1: w = acc0 + 2^-8 acc1 + (levels 2..4) (the first two exactly) into the
-      // staging area, [column][row] so that a warp's stores are contiguous; each thread
-      // reads back only its own entries
-      const uint32_t tbase = c.tmem + ((uint32_t)(q4 * 32) << 16);
-      for (int c0 = cb; c0 < ce; c0 += 8) {            // warp-uniform bounds
-        float acc[NSL][8];
+      // staging units of row rt
+      {
+        const int cb = half * TC_EPI_COLS;              // this warp's columns [cb, cb + 48)
+        const int ce = min(cb + TC_EPI_COLS, nw);
+        const uint32_t tbase = c.tmem + ((uint32_t)(q4 * 32) << 16);
+        uint4* srow = c.staging + rt * TC_SROW;
+        for (int c0 = cb; c0 < ce; c0 += 8) {          // warp-uniform bounds
+          float acc[NSL][8];
 #pragma unroll
-        for (int L = 0; L < NSL; ++L) tc::tmem_ld8(tbase + L * TC_N + c0, acc[L]);
-        tc::tmem_ld_wait();
+          for (int L = 0; L < NSL; ++L) tc::tmem_ld8(tbase + L * TC_N + c0, acc[L]);
+          tc::tmem_ld_wait();
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          float wh, wl;
-          two_sum(acc[0][k], acc[1][k] * (1.f / 256.f), wh, wl);
-          wl = __fadd_rn(wl, __fmaf_rn(acc[4][k], 1.f / 4294967296.f,
-                                       __fmaf_rn(acc[3][k], 1.f / 16777216.f,
-                                                 acc[2][k] * (1.f / 65536.f))));
-          c.staging[(c0 + k) * TC_M + rt] = make_float2(wh, wl);
+          for (int k2 = 0; k2 < 4; ++k2) {
+            float w4[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int k = 2 * k2 + h;
+              float wh, wl;
+              two_sum(acc[0][k], acc[1][k] * (1.f / 256.f), wh, wl);
+              wl = __fadd_rn(wl, __fmaf_rn(acc[4][k], 1.f / 4294967296.f,
+                                           __fmaf_rn(acc[3][k], 1.f / 16777216.f,
+                                                     acc[2][k] * (1.f / 65536.f))));
+              w4[2 * h] = wh;
+              w4[2 * h + 1] = wl;
+            }
+            srow[k2 * TC_CH + c0 / 8] = make_uint4(__float_as_uint(w4[0]), __float_as_uint(w4[1]),
+                                                   __float_as_uint(w4[2]), __float_as_uint(w4[3]));
+          }
         }
       }
       // the accumulators are read: the next tile's MMAs may start
       tc::tc_fence_before();
       tc::mbar_arrive(c.tmem_empty);
       ++st.ept;
-      // phase 2: C = c (alpha Y - A B) from the staged sums, sliced and stored
-      if (row < mp) {
-        for (int c0 = cb; c0 < ce; c0 += 8) {
-          const int j0 = tn * TC_N + c0;
-          const size_t idx0 = (size_t)row * io.ld + j0;
-          float oh[8], ol[8];
-          uint4 yr[NSL];
+      grp_sync<kEpiBar>();                             // staging complete
+      // phase 2: C = c (alpha Y - A B) for (row, 8-column chunk) tasks, consecutive threads
+      // on consecutive chunks of a row
+      for (int task = etid; task < TC_M * TC_CH; task += TC_EPI_WARPS * 32) {
+        const int r = task / TC_CH, ch = task - r * TC_CH;
+        const int row = tm * TC_M + r;
+        if (row >= mp || ch >= nch) continue;
+        const int j0 = tn * TC_N + ch * 8;
+        const size_t idx0 = (size_t)row * io.ld + j0;
+        uint4* su = c.staging + r * TC_SROW + ch;
+        uint4 yr[NSL];
 #pragma unroll
-          for (int k = 0; k < NSL; ++k)
-            yr[k] = *reinterpret_cast<const uint4*>(Y.q + k * io.plane + idx0);
+        for (int k = 0; k < NSL; ++k)
+          yr[k] = *reinterpret_cast<const uint4*>(Y.q + k * io.plane + idx0);
+        float wv[16];
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+          const uint4 u = su[k2 * TC_CH];
+          wv[4 * k2] = __uint_as_float(u.x);
+          wv[4 * k2 + 1] = __uint_as_float(u.y);
+          wv[4 * k2 + 2] = __uint_as_float(u.z);
+          wv[4 * k2 + 3] = __uint_as_float(u.w);
+        }
+        float oh[8], ol[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          float yq[NSL];
+#pragma unroll
+          for (int s2 = 0; s2 < NSL; ++s2)
+            yq[s2] = __half2float(reinterpret_cast<const __half*>(&yr[s2])[k]);
+          // y / 2^(Y.e-15) = ya + yb, exact (ya an integer below 2^16, yb below 1)
+          const float ya = __fmaf_rn(yq[0], 256.f, yq[1]);
+          const float yb = __fmaf_rn(yq[2], 1.f / 256.f, __fmaf_rn(yq[3], 1.f / 65536.f,
+                                                                   yq[4] * (1.f / 16777216.f)));
+          const float wh = wv[2 * k], wl = wv[2 * k + 1];
+          // out = c cscale (alpha' y - w), alpha' = alpha 2^(Y.e-15) / cscale (exact)
+          const float p1 = __fmul_rn(alpha_s, ya);
+          const float e1 = __fmaf_rn(alpha_s, yb, __fmaf_rn(alpha_s, ya, -p1));
+          float d, de;
+          two_sum(p1, -wh, d, de);
+          de = __fadd_rn(de, __fsub_rn(e1, wl));
+          oh[k] = __fmul_rn(c_s, d);
+          ol[k] = __fmaf_rn(c_s, de, __fmaf_rn(c_s, d, -oh[k]));
+        }
+        store8_planes(C.q, io.plane, io.ld, row, j0, oh, ol, C.e, su, tile_mirror);
+        if (flags & EPI_AMAX) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) amax = fmaxf(amax, fabsf(oh[k]));
+        }
+        if (flags & EPI_NORM) {
+          const bool mchunk = tile_mirror && mirror_needed(row, j0 + 7, tm);
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
-            float yq[NSL];
-#pragma unroll
-            for (int s2 = 0; s2 < NSL; ++s2)
-              yq[s2] = __half2float(reinterpret_cast<const __half*>(&yr[s2])[k]);
-            // y / 2^(Y.e-15) = ya + yb, exact (ya an integer below 2^16, yb below 1)
-            const float ya = __fmaf_rn(yq[0], 256.f, yq[1]);
-            const float yb = __fmaf_rn(yq[2], 1.f / 256.f, __fmaf_rn(yq[3], 1.f / 65536.f,
-                                                                     yq[4] * (1.f / 16777216.f)));
-            const float2 w = c.staging[(c0 + k) * TC_M + rt];
-            // out = c cscale (alpha' y - w), alpha' = alpha 2^(Y.e-15) / cscale (exact)
-            const float p1 = __fmul_rn(alpha_s, ya);
-            const float e1 = __fmaf_rn(alpha_s, yb, __fmaf_rn(alpha_s, ya, -p1));
-            float d, de;
-            two_sum(p1, -w.x, d, de);
-            de = __fadd_rn(de, __fsub_rn(e1, w.y));
-            oh[k] = __fmul_rn(c_s, d);
-            ol[k] = __fmaf_rn(c_s, de, __fmaf_rn(c_s, d, -oh[k]));
+            const int jj = j0 + k;
+            const bool in = (row < io.m) && (jj < io.m);
+            const float d = (row == jj) ? 1.f : 0.f;
+            const float ev = in ? __fadd_rn(__fsub_rn(oh[k], d), ol[k]) : 0.f;
+            // a mirrored entry counts twice
+            nrm += (mchunk && mirror_needed(row, jj, tm)) ? 2.f * ev * ev : ev * ev;
           }
-          const unsigned mir = store8_sym(C.q, io.plane, io.ld, row, j0, tm, oh, ol, C.e);
-          if (flags & EPI_AMAX) {
+        }
+      }
+      if (tile_mirror) {
+        grp_sync<kEpiBar>();                           // slices of the tile in the staging area
+        // phase 3: entry (i, j) also at (j, i) where that lies in a skipped tile; a thread
+        // per tile row i and half of the chunks, so a warp writes 32 consecutive columns
+        const int r = etid & (TC_M - 1), hc = etid / TC_M;
+        const int row = tm * TC_M + r;
+        if (row < mp) {
+          for (int ch = hc * (TC_CH / 2); ch < min((hc + 1) * (TC_CH / 2), nch); ++ch) {
+            const int j0 = tn * TC_N + ch * 8;
+            if (!mirror_needed(row, j0 + 7, tm)) continue;
+            const uint4* su = c.staging + r * TC_SROW + ch;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) amax = fmaxf(amax, fabsf(oh[k]));
-          }
-          if (flags & EPI_NORM) {
+            for (int k = 0; k < NSL; ++k) {
+              const uint4 v = su[k * TC_CH];
+              const __half* hv = reinterpret_cast<const __half*>(&v);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const int jj = j0 + k;
-              const bool in = (row < io.m) && (jj < io.m);
-              const float d = (row == jj) ? 1.f : 0.f;
-              const float ev = in ? __fadd_rn(__fsub_rn(oh[k], d), ol[k]) : 0.f;
-              nrm += ((mir >> k) & 1u) ? 2.f * ev * ev : ev * ev;   // a mirrored entry counts twice
+              for (int cc = 0; cc < 8; ++cc) {
+                const int j = j0 + cc;
+                if (mirror_needed(row, j, tm)) C.q[k * io.plane + (size_t)j * io.ld + row] = hv[cc];
+              }
             }
           }
         }
       }
+      grp_sync<kEpiBar>();                             // staging free for the next tile
     }
     if (flags & EPI_NORM) {
       nrm = warp_sum_f(nrm);
-      if (lane == 0) atomicAdd(io.norm2_s, nrm);
+      if (lane == 0) io.norm_part[warp] = nrm;      // warps 0..7
     }
     if (flags & EPI_AMAX) {
       for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
@@ -813,7 +885,7 @@ __device__ void gemm_sync(Mat A, Mat B, Mat C, Mat Y, int flags, const GemmIO& i
   }
   if (flags & EPI_NORM) {
     nrm = warp_sum_f(nrm);
-    if (lane == 0) atomicAdd(io.norm2_s, nrm);
+    if (lane == 0) io.norm_part[warp] = nrm;        // warps 0..7
   }
   if (flags & EPI_AMAX) {
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
@@ -853,7 +925,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(tail);  // full, empty [TC_STAGES], tmem_full, tmem_empty
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tail + 96);
   int* abort_s = reinterpret_cast<int*>(tail + 100);
-  float* norm2_s = reinterpret_cast<float*>(tail + 104);
+  float* norm_part = reinterpret_cast<float*>(tail + 112);   // [kMaxWarps]
   unsigned* amax_s = reinterpret_cast<unsigned*>(tail + 108);
   __shared__ int job_s;
 
@@ -883,7 +955,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     tcx.empty = bars + TC_STAGES;
     tcx.tmem_full = bars + 2 * TC_STAGES;
     tcx.tmem_empty = bars + 2 * TC_STAGES + 1;
-    tcx.staging = reinterpret_cast<float2*>(sm + TC_STAGE_AREA);
+    tcx.staging = reinterpret_cast<uint4*>(sm + TC_STAGE_AREA);
     tcx.abort_s = abort_s;
     tcx.tmem = *tmem_holder;
     tcx.tm_a = &a.tm_a;
@@ -929,8 +1001,6 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     const int mp8 = mp / 8;
     float ih, il;
     split_dbl(inv_lam, ih, il);
-    if (tid == 0) *norm2_s = 0.f;
-    __syncthreads();
     {
       float nrm = 0.f;
       for (int e = tid; e < mp * mp8; e += blockDim.x) {
@@ -951,10 +1021,10 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
         store8_slices(B3[0].q, plane, (size_t)i * LD + j0, mh, ml, e_m);
       }
       nrm = warp_sum_f(nrm);
-      if ((tid & 31) == 0) atomicAdd(norm2_s, nrm);
+      if ((tid & 31) == 0) norm_part[tid >> 5] = nrm;
     }
     __syncthreads();
-    float nrm2 = *norm2_s;
+    float nrm2 = sum_parts(norm_part, nwarps());
 
     // lower end of M_0's spectrum: the raw estimate gives the condition estimate
     // lambda_bar / lambda_min(S) = 1 / lambda_min(M_0), half of it steers the steps
@@ -979,7 +1049,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     __threadfence();             // planes are read next through L2 (cp.async.cg / TMA)
     __syncthreads();
 
-    GemmIO io{mp, m, p, LD, plane, norm2_s, amax_s, 0.f, 0.f};
+    GemmIO io{mp, m, p, LD, plane, norm_part, amax_s, 0.f, 0.f};
     // vt: vector work to run with this GEMM (tcgen05: on the epilogue warps while the MMA
     // warp starts; mma.sync: before the GEMM on all warps)
     auto gemm = [&](Mat A, Mat B, Mat C, Mat Y, int flags, const VecTask* vt) -> bool {
@@ -1048,10 +1118,6 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
       for (int s = 1; s <= p; ++s) {
         const bool last = (s == p);
         B3[dst].e = last ? e_m : exp_of(partial_bound(st, s)) + eb;
-        if (last) {
-          if (tid == 0) *norm2_s = 0.f;
-          __syncthreads();
-        }
         if (!gemm(Mk, B3[src], B3[dst], B3[src], last ? EPI_NORM : 0,
                   (track && s == 1) ? &vt : nullptr)) {
           stop = true;
@@ -1065,8 +1131,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
       mi = src;
       lo = st.lo_next;
       ++iters;
-      nrm2 = *norm2_s;
-      __syncthreads();
+      nrm2 = sum_parts(norm_part, kEpiGroupWarps);  // the GEMM ended with a block barrier
       if (!(nrm2 == nrm2) || nrm2 > 1e30f) { bad = true; break; }
       if (nrm2 <= tol2 || iters >= a.k_max) break;
       // at the rounding-error floor (only after a Newton step: a scaled step maps the

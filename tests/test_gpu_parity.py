@@ -241,6 +241,18 @@ def test_graph_and_stream_paths_agree(sm):
     assert torch.equal(y1, y2)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_repeat_runs_bitwise_equal(sm, precision):
+    """Every reduction that steers the iteration (norms, maxima) is taken in a fixed order,
+    so repeated calls give identical bits (orders 40..250: ragged tiles and mirror images)."""
+    a = wl.overlap_uniform(n=1500)
+    v = torch.tensor(a.vals, device="cuda")
+    plan = sm.submat_plan(a.rowptr, a.colind, 2, precision=precision, use_graph=False)
+    ys = [sm.submat_invroot(plan, v, sync=True) for _ in range(3)]
+    for y in ys[1:]:
+        assert torch.equal(ys[0], y)
+
+
 def test_device_pattern_input(sm):
     a = wl.overlap_small(n=700)
     rp = torch.tensor(a.rowptr, device="cuda")
