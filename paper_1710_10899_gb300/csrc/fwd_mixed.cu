@@ -45,7 +45,9 @@
 // Working matrices live in a per-CTA global scratch: 34 planes of LD x LD halves per CTA
 // (LD = the plan's largest order padded to 64): X, T, M (two buffers each) x 5 planes, then
 // the gathered S_j in FP64 in the last four planes' space.  A submatrix of order m uses the
-// leading mp x mp block (mp = m padded to 64); its padding rows/columns stay exactly zero.
+// leading mp x mp block (mp = m padded to 16 for tcgen05, 64 for mma.sync); its padding
+// rows/columns stay exactly zero.  Rows of a tile beyond mp may hold older data: they only
+// reach output entries beyond mp, which are never stored.
 #include <cuda_fp16.h>
 #include "common.cuh"
 #include "refine.cuh"
@@ -360,8 +362,8 @@ __device__ float start_lo_slices(const __half* q, size_t plane, int ld, int e, i
 // ======================================================================================
 // tcgen05 engine
 // ======================================================================================
-// Output tiles of 128 rows x 96 columns (the last column tile of a row block is 32, 64 or 96
-// wide: padded orders are multiples of 64).  A tcgen05.mma costs a fixed ~45 cycles below
+// Output tiles of 128 rows x 96 columns (the last column tile of a row block is 16 to 96
+// wide: padded orders are multiples of 16).  A tcgen05.mma costs a fixed ~45 cycles below
 // N ~ 96 (measured), so 96-wide tiles keep the tensor pipe on the work instead of the
 // overhead.  The five 96-column level accumulators fill one 480-column TMEM buffer; the
 // epilogue drains it in phases: phase 1 (a thread per TMEM lane, i.e. per tile row)
@@ -512,7 +514,7 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
       for (int t = 0; t < ntiles && !*c.abort_s; ++t) {
         int tm, tn;
         tc_tile(t, ntn, tm, tn);
-        const int nw = min(TC_N, mp - tn * TC_N);      // 96, or 64 / 32 for the last tile
+        const int nw = min(TC_N, mp - tn * TC_N);      // 96, or 16..80 for the last tile
         const uint32_t idesc = tc::idesc_f16(TC_M, nw);
         // the single accumulator buffer is free once the epilogue has read the previous tile
         if (st.tmt >= 1 && !tc::mbar_wait(c.tmem_empty, (st.tmt - 1) & 1, TC_WAIT_LIMIT)) {
@@ -975,7 +977,9 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     const int m = a.m[j];
     const int pos = a.pos[j];
     const int p = a.p;
-    const int mp = pad_mixed(m);
+    // padded order: the tcgen05 engine needs multiples of its 16-wide k-step (and of 16 for
+    // an MMA's N), the mma.sync engine multiples of its 64 x 64 tiles
+    const int mp = TC ? (m + 15) / 16 * 16 : pad_mixed(m);
 
     // Two X buffers (p = 1 only) and three buffers for M_k and the partial products T^s M_k
     // (M_k is the A operand of all p products of an iteration and stays in place).
