@@ -150,13 +150,31 @@ __device__ __forceinline__ float abs_f32_approx(double v) {
   return __int_as_float((int)(((unsigned)(ex - 1023 + 127) << 23) | ((hi & 0xFFFFFu) << 3)));
 }
 
+// Positions of U keys in the sorted a[0..len) (or -1), by a branchless bisection whose U
+// chains run interleaved (each step is U independent shared-memory reads).  Keys < 0 give -1.
+template <int U>
+__device__ __forceinline__ void find_sorted_u(const int32_t* a, int len, const int* key,
+                                              int* pos) {
+  int base[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) base[u] = 0;
+  for (int n = len; n > 1;) {
+    const int half = n >> 1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) base[u] = (a[base[u] + half] <= key[u]) ? base[u] + half : base[u];
+    n -= half;
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) pos[u] = (key[u] >= 0 && len > 0 && a[base[u]] == key[u]) ? base[u] : -1;
+}
+
 // Algorithm 1 for row j (value part): S[k*m + l] = A[R[k]][R[l]] in FP64 (zero where not
 // stored), R staged in shared memory (R_s, m ints), and the Gershgorin bound
 // max_k sum_l |S_kl| returned to every thread (summed in FP32 and enlarged by 1e-4, which
 // covers the rounding; any bound above the largest eigenvalue serves).  The extents of all
-// m pattern rows are loaded first, in parallel; then each warp takes one row at a time and
-// loads up to eight 32-entry chunks of it before searching, so that a row costs one round
-// trip to memory.  red_s: kRedDoubles doubles of shared memory.
+// m pattern rows are loaded first, in parallel; then each warp takes one row at a time, with
+// the first 32 U entries of its next row already requested, and locates a row's entries in
+// R by interleaved bisections.  red_s: kRedDoubles doubles of shared memory.
 static __device__ double gather_submatrix(const int32_t* __restrict__ rowptr,
                                    const int32_t* __restrict__ colind,
                                    const double* __restrict__ vals, int j, int m,
@@ -174,26 +192,41 @@ static __device__ double gather_submatrix(const int32_t* __restrict__ rowptr,
   float wmax = 0.f;
   const int nw = nwarps();
   constexpr int U = 8;
+  int ncol[U];
+  double nv[U];
+  auto load_chunk = [&](int e0, int e_end, int* col, double* v) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * 32 + lane;
+      col[u] = e < e_end ? colind[e] : -1;
+      v[u] = e < e_end ? vals[e] : 0.0;
+    }
+  };
+  if (warp < m) load_chunk(ext_s[warp].x, ext_s[warp].y, ncol, nv);
   for (int k = warp; k < m; k += nw) {
     const int b = ext_s[k].x, e_end = ext_s[k].y;
+    int col[U];
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      col[u] = ncol[u];
+      v[u] = nv[u];
+    }
+    if (k + nw < m) load_chunk(ext_s[k + nw].x, ext_s[k + nw].y, ncol, nv);   // next row
     float sum = 0.f;
-    for (int e0 = b; e0 < e_end; e0 += 32 * U) {
-      int col[U];
-      double v[U];
+    for (int e0 = b;;) {
+      int l[U];
+      find_sorted_u<U>(R_s, m, col, l);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int e = e0 + u * 32 + lane;
-        col[u] = e < e_end ? colind[e] : -1;
-        v[u] = e < e_end ? vals[e] : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int l = col[u] >= 0 ? find_sorted(R_s, m, col[u]) : -1;
-        if (l >= 0) {
-          S[k * m + l] = v[u];
+        if (l[u] >= 0) {
+          S[k * m + l[u]] = v[u];
           sum += abs_f32_approx(v[u]);
         }
       }
+      e0 += 32 * U;
+      if (e0 >= e_end) break;
+      load_chunk(e0, e_end, col, v);                 // rows longer than 32 U entries
     }
     sum = warp_sum_f(sum);
     // a NaN row sum must survive the max

@@ -669,39 +669,39 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
           for (int k = 0; k < 8; ++k) amax = fmaxf(amax, fabsf(oh[k]));
         }
         if (flags & EPI_NORM) {
-          const bool mchunk = tile_mirror && mirror_needed(row, j0 + 7, tm);
+          // the whole chunk is mirrored or none of it (chunks never straddle a row block)
+          const bool mchunk = tile_mirror && mirror_needed(row, j0, tm);
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const int jj = j0 + k;
             const bool in = (row < io.m) && (jj < io.m);
             const float d = (row == jj) ? 1.f : 0.f;
             const float ev = in ? __fadd_rn(__fsub_rn(oh[k], d), ol[k]) : 0.f;
-            // a mirrored entry counts twice
-            nrm += (mchunk && mirror_needed(row, jj, tm)) ? 2.f * ev * ev : ev * ev;
+            nrm += mchunk ? 2.f * ev * ev : ev * ev;   // a mirrored entry counts twice
           }
         }
       }
       if (tile_mirror) {
         grp_sync<kEpiBar>();                           // slices of the tile in the staging area
-        // phase 3: entry (i, j) also at (j, i) where that lies in a skipped tile; a thread
-        // per tile row i and half of the chunks, so a warp writes 32 consecutive columns
-        const int r = etid & (TC_M - 1), hc = etid / TC_M;
-        const int row = tm * TC_M + r;
-        if (row < mp) {
-          for (int ch = hc * (TC_CH / 2); ch < min((hc + 1) * (TC_CH / 2), nch); ++ch) {
-            const int j0 = tn * TC_N + ch * 8;
-            if (!mirror_needed(row, j0 + 7, tm)) continue;
-            const uint4* su = c.staging + r * TC_SROW + ch;
+        // phase 3: entry (i, j) also at (j, i) where that lies in a skipped tile.  A task is
+        // a chunk of 8 columns reaching a later row block times 32 tile rows (one warp, a
+        // lane per row, so each store covers 32 consecutive columns); whether a chunk is
+        // mirrored depends only on its row block (chunks never straddle one) and on the rows'
+        // 96-column tile (32 aligned rows never straddle one), so tasks are warp-uniform.
+        const int ch_lo = max(0, ((tm + 1) * TC_M - tn * TC_N) / 8);
+        const int ntask = (nch - ch_lo) * (TC_M / 32);
+        for (int task = warp; task < ntask; task += TC_EPI_WARPS) {
+          const int ch = ch_lo + task / (TC_M / 32), r = (task % (TC_M / 32)) * 32 + lane;
+          const int row = tm * TC_M + r, j0 = tn * TC_N + ch * 8;
+          if (row >= mp || !mirror_needed(row, j0, tm)) continue;
+          const uint4* su = c.staging + r * TC_SROW + ch;
 #pragma unroll
-            for (int k = 0; k < NSL; ++k) {
-              const uint4 v = su[k * TC_CH];
-              const __half* hv = reinterpret_cast<const __half*>(&v);
+          for (int k = 0; k < NSL; ++k) {
+            const uint4 v = su[k * TC_CH];
+            const __half* hv = reinterpret_cast<const __half*>(&v);
+            __half* dst = C.q + k * io.plane + (size_t)j0 * io.ld + row;
 #pragma unroll
-              for (int cc = 0; cc < 8; ++cc) {
-                const int j = j0 + cc;
-                if (mirror_needed(row, j, tm)) C.q[k * io.plane + (size_t)j * io.ld + row] = hv[cc];
-              }
-            }
+            for (int cc = 0; cc < 8; ++cc) dst[(size_t)cc * io.ld] = hv[cc];
           }
         }
       }
