@@ -109,17 +109,23 @@ __device__ __forceinline__ void store8_slices(__half* q, size_t plane, size_t id
     *reinterpret_cast<uint4*>(q + k * plane + idx0) = *reinterpret_cast<const uint4*>(out[k]);
 }
 
-// Barrier of a warp group: BAR = 0 is the whole block (__syncthreads); BAR = kEpiBar is the
-// tcgen05 engine's epilogue warps 0..kEpiGroupWarps-1 (a named barrier), which run vector
-// work while the MMA and TMA warps run a GEMM.
-constexpr int kEpiBar = 3;
-constexpr int kEpiGroupWarps = 8;
+// Warp groups of the tcgen05 CTA, each with a named barrier: BAR = 0 is the whole block
+// (__syncthreads); kGemmBar the warps that run a GEMM (epilogue, TMA, MMA: 0..9); kEpiBar
+// the epilogue warps 0..7; kVecBar the two vector warps 10..11, which apply an iteration's
+// step to the carried vectors while the other warps run that iteration's GEMMs.
+constexpr int kGemmBar = 1, kGemmWarps = 10;
+constexpr int kVecBar = 2, kVecWarp0 = 10, kVecGroupWarps = 2;
+constexpr int kEpiBar = 3, kEpiGroupWarps = 8;
+template <int BAR>
+__device__ __forceinline__ constexpr int grp_count() {
+  return BAR == kGemmBar ? kGemmWarps * 32 : BAR == kVecBar ? kVecGroupWarps * 32 : kEpiGroupWarps * 32;
+}
 template <int BAR>
 __device__ __forceinline__ void grp_sync() {
   if (BAR == 0)
     __syncthreads();
   else
-    asm volatile("bar.sync %0, %1;\n" ::"n"(BAR), "n"(kEpiGroupWarps * 32) : "memory");
+    asm volatile("bar.sync %0, %1;\n" ::"n"(BAR), "n"(grp_count<BAR>()) : "memory");
 }
 // Barrier of the epilogue warps that also returns whether any of them passed true.
 __device__ __forceinline__ bool epi_sync_any(bool v) {
@@ -140,9 +146,16 @@ __device__ __forceinline__ float sum_parts(const float* part, int n) {
   return r;
 }
 template <int BAR>
-__device__ __forceinline__ int grp_warps() { return BAR == 0 ? nwarps() : kEpiGroupWarps; }
+__device__ __forceinline__ int grp_threads() { return BAR == 0 ? (int)blockDim.x : grp_count<BAR>(); }
 template <int BAR>
-__device__ __forceinline__ int grp_threads() { return BAR == 0 ? (int)blockDim.x : kEpiGroupWarps * 32; }
+__device__ __forceinline__ int grp_warps() { return grp_threads<BAR>() >> 5; }
+// thread and warp index within the group
+template <int BAR>
+__device__ __forceinline__ int grp_tid() {
+  return BAR == kVecBar ? (int)threadIdx.x - kVecWarp0 * 32 : (int)threadIdx.x;
+}
+template <int BAR>
+__device__ __forceinline__ int grp_warp() { return grp_tid<BAR>() >> 5; }
 
 // y[i] = scale * sum_k X(i,k) x[k] for i < m, X from its first NP planes (FP32 result).
 // Each warp takes RW rows at a time (their loads are in flight together), eight consecutive
@@ -150,7 +163,7 @@ __device__ __forceinline__ int grp_threads() { return BAR == 0 ? (int)blockDim.x
 template <int NP, int RW = 4, int BAR = 0>
 __device__ void matvec_slices_f32(const __half* q, size_t plane, int ld, float scale,
                                   const float* x, float* y, int m, int mp) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = grp_warp<BAR>();
   for (int i0 = warp * RW; i0 < m; i0 += grp_warps<BAR>() * RW) {
     float acc[RW];
 #pragma unroll
@@ -198,7 +211,7 @@ template <int RW = 2, int BAR = 0>
 __device__ void matvec2_slices(const __half* q, size_t plane, int ld, int e, const float* xh,
                                const float* xl, double* out, const float* u, float* uo, int m,
                                int mp) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = grp_warp<BAR>();
   const double sc = ldexp(1.0, e - 15);
   for (int i0 = warp * RW; i0 < m; i0 += grp_warps<BAR>() * RW) {
     float sh[RW], sl[RW], su[RW];
@@ -273,7 +286,7 @@ struct VecTask {
 
 template <int BAR>
 __device__ void vec_task(const VecTask& v) {
-  const int gt = threadIdx.x, gn = grp_threads<BAR>();
+  const int gt = grp_tid<BAR>(), gn = grp_threads<BAR>();
   const float cf = (float)v.c, af = (float)v.alpha;
   for (int t = 0; t < v.p; ++t) {
     if (t < v.ny) {
@@ -395,9 +408,11 @@ constexpr uint32_t TC_TMEM_COLS = 512;
 static_assert(TC_BUF_COLS <= (int)TC_TMEM_COLS, "TMEM budget");
 static_assert(TC_STAGE_BYTES % 1024 == 0 || TC_STAGE_BYTES % 256 == 0, "swizzle atoms");
 // tcgen05 CTA: warps 0-7 run the epilogue (warp w: TMEM lane quarter w % 4, column half
-// w / 4 of the tile), warp 8 issues TMA, warp 9 issues MMAs.
+// w / 4 of the tile), warp 8 issues TMA, warp 9 issues MMAs, warps 10-11 run the vector
+// steps (12 warps keep the 168-register budget of 10).
 constexpr int TC_EPI_WARPS = kEpiGroupWarps;
-constexpr int TC_THREADS = (TC_EPI_WARPS + 2) * 32;
+constexpr int TC_THREADS = (kVecWarp0 + kVecGroupWarps) * 32;
+static_assert(kGemmWarps == TC_EPI_WARPS + 2 && kVecWarp0 == kGemmWarps, "warp roles");
 constexpr int TC_TMA_WARP = TC_EPI_WARPS, TC_MMA_WARP = TC_EPI_WARPS + 1;
 constexpr int TC_EPI_COLS = TC_N * 4 / TC_EPI_WARPS;  // tile columns per epilogue warp (48)
 
@@ -471,9 +486,14 @@ __device__ __forceinline__ void store8_planes(__half* q, size_t plane, int ld, i
 }
 
 // C = A B^T on the tcgen05 engine (see the header comment).  All TC_THREADS threads call it.
-// Returns false if a pipeline wait timed out (the CTA then stops).
+// The GEMMs of one iteration run back to back with the GEMM warps' barrier between them;
+// full_in / full_out make the first one start and the last one end with a whole-block
+// barrier, between which the vector warps run the iteration's vector step vt (given with the
+// first GEMM; it reads only M_k, the A operand of all of them, and the carried vectors).
+// Returns false if a pipeline wait timed out (the CTA then stops); a time-out in a GEMM that
+// does not end with full_out is reported by the iteration's last GEMM.
 __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y, int flags,
-                        const GemmIO& io, const VecTask* vt) {
+                        const GemmIO& io, const VecTask* vt, bool full_in, bool full_out) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mp = io.mp;
   const int ntm = (mp + TC_M - 1) / TC_M, ntn = (mp + TC_N - 1) / TC_N, KT = mp / TC_K;
@@ -481,7 +501,16 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
   // generic-proxy writes (planes, shared vectors) before async-proxy reads/writes
   tc::fence_proxy_async_global();
   tc::fence_proxy_async_shared();
-  __syncthreads();
+  if (warp >= kVecWarp0) {                             // ---- vector warps
+    if (full_in) {
+      __syncthreads();
+      if (vt) vec_task<kVecBar>(*vt);
+    }
+    if (!full_out) return true;
+    __syncthreads();
+    return *c.abort_s == 0;
+  }
+  if (full_in) __syncthreads(); else grp_sync<kGemmBar>();
 
   if (warp == TC_TMA_WARP) {
     if (lane == 0) {                                   // ---- TMA producer
@@ -559,9 +588,6 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
       }
     }
   } else {                                             // ---- epilogue (TMEM lanes 0..127)
-    // vector work handed to this GEMM: the MMA warp fills the first accumulator buffers
-    // meanwhile
-    if (vt) vec_task<kEpiBar>(*vt);
     const int q4 = warp & 3, half = warp >> 2;
     const int etid = tid;                              // 0 .. 255 (warps 0..7)
     // the level sums count in units of cscale = 2^(A.e + B.e - 14), Y's planes in units of
@@ -571,8 +597,9 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
     float nrm = 0.f, amax = 0.f;
     const int rt = q4 * 32 + lane;                    // phase 1: this thread's tile row
     for (int t = 0; t < ntiles; ++t) {
-      // the epilogue warps meet at barriers below, so they leave together
-      const bool timed_out = !tc::mbar_wait(c.tmem_full, st.ept & 1, TC_WAIT_LIMIT);
+      // the epilogue warps meet at barriers below, so they leave together (at once if an
+      // earlier GEMM of the iteration already gave up)
+      const bool timed_out = *c.abort_s || !tc::mbar_wait(c.tmem_full, st.ept & 1, TC_WAIT_LIMIT);
       if (epi_sync_any(timed_out)) {
         *c.abort_s = 1;
         break;
@@ -719,6 +746,10 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
   // the planes written here are read next by TMA (async proxy) through L2
   __threadfence();
   tc::fence_proxy_async_global();
+  if (!full_out) {
+    grp_sync<kGemmBar>();
+    return true;
+  }
   __syncthreads();
   return *c.abort_s == 0;
 }
@@ -1054,10 +1085,12 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     __syncthreads();
 
     GemmIO io{mp, m, p, LD, plane, norm_part, amax_s, 0.f, 0.f};
-    // vt: vector work to run with this GEMM (tcgen05: on the epilogue warps while the MMA
-    // warp starts; mma.sync: before the GEMM on all warps)
-    auto gemm = [&](Mat A, Mat B, Mat C, Mat Y, int flags, const VecTask* vt) -> bool {
-      if (TC) return gemm_tc(tcx, tst, A, B, C, Y, flags, io, vt);
+    // vt: vector work to run with this GEMM (tcgen05: on the vector warps during this and
+    // the iteration's later GEMMs; mma.sync: before the GEMM on all warps).  first / last:
+    // the GEMM starts / ends an iteration's sequence (see gemm_tc).
+    auto gemm = [&](Mat A, Mat B, Mat C, Mat Y, int flags, const VecTask* vt, bool first = true,
+                    bool last = true) -> bool {
+      if (TC) return gemm_tc(tcx, tst, A, B, C, Y, flags, io, vt, first, last);
       if (vt) vec_task<0>(*vt);
       gemm_sync(A, B, C, Y, flags, io, reinterpret_cast<__half*>(sm));
       return true;
@@ -1123,7 +1156,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
         const bool last = (s == p);
         B3[dst].e = last ? e_m : exp_of(partial_bound(st, s)) + eb;
         if (!gemm(Mk, B3[src], B3[dst], B3[src], last ? EPI_NORM : 0,
-                  (track && s == 1) ? &vt : nullptr)) {
+                  (track && s == 1) ? &vt : nullptr, s == 1, last)) {
           stop = true;
           break;
         }
