@@ -385,23 +385,23 @@ __device__ float start_lo_slices(const __half* q, size_t plane, int ld, int e, i
 // consecutive threads to consecutive 8-column chunks of a row, so a warp's global loads and
 // stores cover whole row segments instead of 32 rows; phase 3 writes the mirror images of
 // the entries that fall in skipped tiles (see tc_skip) from the slices left in shared
-// memory, a thread per tile row, so that those stores are contiguous too.  Operands move by
-// TMA in 16-wide k-slices (32-byte rows, SWIZZLE_32B) through a 2-stage mbarrier pipeline
-// (a third stage measured no faster, and the staging area needs the room).
+// memory (the last plane re-read from C), a thread per tile row, so that those stores are
+// contiguous too.  Operands move by TMA in 16-wide k-slices (32-byte rows, SWIZZLE_32B)
+// through a 3-stage mbarrier pipeline.
 constexpr int TC_M = 128, TC_N = 96, TC_K = 16;        // tile and k-slice
-constexpr int TC_STAGES = 2;
+constexpr int TC_STAGES = 3;
 constexpr int TC_A_PLANE = TC_M * TC_K * 2;            // 4096 B
 constexpr int TC_B_PLANE = TC_N * TC_K * 2;            // 3072 B
 constexpr int TC_STAGE_BYTES = NSL * (TC_A_PLANE + TC_B_PLANE);   // 35840 B
-constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 71680 B
-// Staging area: per tile row, NSL x TC_CH 16-byte units (unit (k, ch) of row r holds the
-// double-floats of entries (r, 8 ch + 2k), (r, 8 ch + 2k + 1) for k < 4 after phase 1, and
-// plane k of entries (r, 8 ch .. 8 ch + 7) after phase 2), plus one unit of padding: the odd
-// row stride makes a thread-per-row access (phases 1 and 3) and a thread-per-chunk access
+constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 107520 B
+// Staging area: per tile row, 4 x TC_CH 16-byte units (unit (k, ch) of row r holds the
+// double-floats of entries (r, 8 ch + 2k), (r, 8 ch + 2k + 1) after phase 1, and plane k < 4
+// of entries (r, 8 ch .. 8 ch + 7) after phase 2), plus one unit of padding: the odd row
+// stride makes a thread-per-row access (phases 1 and 3) and a thread-per-chunk access
 // (phase 2) both free of bank conflicts.
 constexpr int TC_CH = TC_N / 8;                        // 8-column chunks per tile row (12)
-constexpr int TC_SROW = NSL * TC_CH + 1;               // units per staged row (61)
-constexpr int TC_STAGING_BYTES = TC_M * TC_SROW * 16;  // 124928 B
+constexpr int TC_SROW = 4 * TC_CH + 1;                 // units per staged row (49)
+constexpr int TC_STAGING_BYTES = TC_M * TC_SROW * 16;  // 100352 B
 constexpr int TC_BUF_COLS = NSL * TC_N;                // 480 TMEM columns
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;           // polls before a wait gives up
 constexpr uint32_t TC_TMEM_COLS = 512;
@@ -464,7 +464,7 @@ __device__ __forceinline__ bool mirror_needed(int i, int j, int tm) {
 }
 
 // Planes of the eight entries (row, j0..j0+7): one 16-byte store per plane to C, and the
-// same planes to the staging units su[0], su[TC_CH], ... when keep (for the mirror pass).
+// planes 0..3 to the staging units su[0], su[TC_CH], ... when keep (for the mirror pass).
 __device__ __forceinline__ void store8_planes(__half* q, size_t plane, int ld, int row, int j0,
                                               const float* vh, const float* vl, int e,
                                               uint4* su, bool keep) {
@@ -481,7 +481,7 @@ __device__ __forceinline__ void store8_planes(__half* q, size_t plane, int ld, i
   for (int k = 0; k < NSL; ++k) {
     const uint4 v = *reinterpret_cast<const uint4*>(out[k]);
     *reinterpret_cast<uint4*>(q + k * plane + idx0) = v;
-    if (keep) su[k * TC_CH] = v;
+    if (keep && k < 4) su[k * TC_CH] = v;
   }
 }
 
@@ -724,7 +724,11 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
           const uint4* su = c.staging + r * TC_SROW + ch;
 #pragma unroll
           for (int k = 0; k < NSL; ++k) {
-            const uint4 v = su[k * TC_CH];
+            // planes 0..3 from the staging area, plane 4 from C (written in phase 2, before
+            // the group barrier)
+            const uint4 v = k < 4 ? su[k * TC_CH]
+                                  : *reinterpret_cast<const uint4*>(C.q + 4 * io.plane +
+                                                                    (size_t)row * io.ld + j0);
             const __half* hv = reinterpret_cast<const __half*>(&v);
             __half* dst = C.q + k * io.plane + (size_t)j0 * io.ld + row;
 #pragma unroll
