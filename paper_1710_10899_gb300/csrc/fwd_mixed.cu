@@ -301,7 +301,7 @@ __device__ void vec_task(const VecTask& v) {
       matvec2_slices<2, BAR>(v.q, v.plane, v.ld, v.e, v.yh, v.yl, v.my, v.u, v.t, v.m, v.mp);
       for (int i = gt; i < v.m; i += gn) v.y[i] = v.c * (v.alpha * v.y[i] - v.my[i]);
     } else {
-      matvec_slices_f32<3, 4, BAR>(v.q, v.plane, v.ld, ldexpf(1.f, v.e - 7), v.u, v.t, v.m, v.mp);
+      matvec_slices_f32<3, 8, BAR>(v.q, v.plane, v.ld, ldexpf(1.f, v.e - 7), v.u, v.t, v.m, v.mp);
     }
     for (int i = gt; i < v.m; i += gn) v.u[i] = cf * (af * v.u[i] - v.t[i]);
     grp_sync<BAR>();
