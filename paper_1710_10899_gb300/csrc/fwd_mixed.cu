@@ -207,7 +207,7 @@ __device__ void matvec_slices_f32(const __half* q, size_t plane, int ld, float s
 // (a = q0 2^8 + q1, b = q2 2^16 + q3 2^8 + q4, A = 2^(e-15) (a + 2^-24 b)) and the products
 // a xh are accumulated error-free in double-float, so out keeps about 44 bits.  Each warp
 // takes RW rows at a time, eight consecutive columns per lane.
-template <int RW = 2, int BAR = 0>
+template <int RW = 2, int BAR = 0, bool U = true>
 __device__ void matvec2_slices(const __half* q, size_t plane, int ld, int e, const float* xh,
                                const float* xl, double* out, const float* u, float* uo, int m,
                                int mp) {
@@ -227,7 +227,7 @@ __device__ void matvec2_slices(const __half* q, size_t plane, int ld, int e, con
       }
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        const float x = xh[c0 + c], xlo = xl[c0 + c], uv = u[c0 + c];
+        const float x = xh[c0 + c], xlo = xl[c0 + c], uv = U ? u[c0 + c] : 0.f;
 #pragma unroll
         for (int r = 0; r < RW; ++r) {
           float qq[NSL];
@@ -241,7 +241,7 @@ __device__ void matvec2_slices(const __half* q, size_t plane, int ld, int e, con
           float t;
           two_sum(sh[r], pr, sh[r], t);
           sl[r] = __fadd_rn(sl[r], __fadd_rn(t, __fmaf_rn(a, xlo, __fmaf_rn(b * (1.f / 16777216.f), x, pe))));
-          su[r] = __fmaf_rn(__fmaf_rn(qq[2], 1.f / 256.f, a), uv, su[r]);   // FP32, 3 planes
+          if (U) su[r] = __fmaf_rn(__fmaf_rn(qq[2], 1.f / 256.f, a), uv, su[r]);   // FP32, 3 planes
         }
       }
     }
@@ -251,14 +251,14 @@ __device__ void matvec2_slices(const __half* q, size_t plane, int ld, int e, con
       for (int o = 16; o > 0; o >>= 1) {
         const float oh = __shfl_xor_sync(0xffffffffu, h, o);
         const float ol = __shfl_xor_sync(0xffffffffu, l, o);
-        uu += __shfl_xor_sync(0xffffffffu, uu, o);
+        if (U) uu += __shfl_xor_sync(0xffffffffu, uu, o);
         float t;
         two_sum(h, oh, h, t);
         l = __fadd_rn(l, __fadd_rn(ol, t));
       }
       if (lane == 0 && i0 + r < m) {
         out[i0 + r] = ((double)h + (double)l) * sc;
-        uo[i0 + r] = uu * (float)sc;
+        if (U) uo[i0 + r] = uu * (float)sc;
       }
     }
   }
@@ -266,10 +266,10 @@ __device__ void matvec2_slices(const __half* q, size_t plane, int ld, int e, con
 }
 
 // The step T = c (alpha I - M_k) applied to the vectors carried for p >= 2: y <- T^ny y (FP64
-// results of double-float products), u <- T^p u (FP32).  All vectors live in the CTA's
-// global scratch and are zero beyond m up to mp.  Run by a warp group (BAR, see grp_sync):
-// inside the tcgen05 engine the epilogue warps do it while the MMA warp starts the
-// iteration's first GEMM, which reads M_k as well but writes elsewhere.
+// results of double-float products) and, with track_u, u <- T^p u (FP32).  All vectors live
+// in the CTA's global scratch and are zero beyond m up to mp.  Run by a warp group (BAR, see
+// grp_sync): inside the tcgen05 engine the vector warps do it during the iteration's GEMMs,
+// which read M_k as well but write elsewhere.
 struct VecTask {
   const __half* q;          // M_k's planes
   size_t plane;
@@ -282,13 +282,14 @@ struct VecTask {
   float* yl;
   double* my;               // scratch: M y
   float* t;                 // scratch: M u
+  bool track_u;             // also u <- T^p u (else y only)
 };
 
 template <int BAR>
 __device__ void vec_task(const VecTask& v) {
   const int gt = grp_tid<BAR>(), gn = grp_threads<BAR>();
   const float cf = (float)v.c, af = (float)v.alpha;
-  for (int t = 0; t < v.p; ++t) {
+  for (int t = 0; t < (v.track_u ? v.p : v.ny); ++t) {
     if (t < v.ny) {
       // M y (FP64) and M u (FP32) in one pass
       for (int i = gt; i < v.mp; i += gn) {
@@ -298,8 +299,15 @@ __device__ void vec_task(const VecTask& v) {
         v.yl[i] = l;
       }
       grp_sync<BAR>();
-      matvec2_slices<2, BAR>(v.q, v.plane, v.ld, v.e, v.yh, v.yl, v.my, v.u, v.t, v.m, v.mp);
+      if (v.track_u)
+        matvec2_slices<2, BAR, true>(v.q, v.plane, v.ld, v.e, v.yh, v.yl, v.my, v.u, v.t, v.m, v.mp);
+      else
+        matvec2_slices<2, BAR, false>(v.q, v.plane, v.ld, v.e, v.yh, v.yl, v.my, v.u, v.t, v.m, v.mp);
       for (int i = gt; i < v.m; i += gn) v.y[i] = v.c * (v.alpha * v.y[i] - v.my[i]);
+      if (!v.track_u) {
+        grp_sync<BAR>();
+        continue;
+      }
     } else {
       matvec_slices_f32<3, 8, BAR>(v.q, v.plane, v.ld, ldexpf(1.f, v.e - 7), v.u, v.t, v.m, v.mp);
     }
@@ -1041,23 +1049,39 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     float ih, il;
     split_dbl(inv_lam, ih, il);
     {
+      // two chunks per thread and step, their loads in flight together
       float nrm = 0.f;
-      for (int e = tid; e < mp * mp8; e += blockDim.x) {
-        const int i = e / mp8, j0 = (e % mp8) * 8;
-        float mh[8], ml[8];
+      const int total = mp * mp8, nt = blockDim.x;
+      for (int e0 = tid; e0 < total; e0 += 2 * nt) {
+        double sv[2][8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int jj = j0 + c;
-          mh[c] = ml[c] = 0.f;
-          if (i < m && jj < m) {
-            float sh, sl;
-            split_dbl(S[i * m + jj], sh, sl);
-            mul_df(sh, sl, ih, il, mh[c], ml[c]);
-            const float ev = __fadd_rn(__fsub_rn(mh[c], i == jj ? 1.f : 0.f), ml[c]);
-            nrm += ev * ev;
-          }
+        for (int h = 0; h < 2; ++h) {
+          const int e = e0 + h * nt;
+          const int i = e / mp8, j0 = (e % mp8) * 8;
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            sv[h][c] = (e < total && i < m && j0 + c < m) ? S[i * m + j0 + c] : 0.0;
         }
-        store8_slices(B3[0].q, plane, (size_t)i * LD + j0, mh, ml, e_m);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int e = e0 + h * nt;
+          if (e >= total) break;
+          const int i = e / mp8, j0 = (e % mp8) * 8;
+          float mh[8], ml[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int jj = j0 + c;
+            mh[c] = ml[c] = 0.f;
+            if (i < m && jj < m) {
+              float sh, sl;
+              split_dbl(sv[h][c], sh, sl);
+              mul_df(sh, sl, ih, il, mh[c], ml[c]);
+              const float ev = __fadd_rn(__fsub_rn(mh[c], i == jj ? 1.f : 0.f), ml[c]);
+              nrm += ev * ev;
+            }
+          }
+          store8_slices(B3[0].q, plane, (size_t)i * LD + j0, mh, ml, e_m);
+        }
       }
       nrm = warp_sum_f(nrm);
       if ((tid & 31) == 0) norm_part[tid >> 5] = nrm;
@@ -1073,7 +1097,8 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
                                          reinterpret_cast<float*>(red_s));
     float lo = 0.5f * lo_raw;
 
-    // tracked vectors (p >= 2): y_0 = e_pos, u_0 = M_0 e_pos
+    // tracked vector (p >= 2): the column y of X (the residual vector u is formed after the
+    // last iteration, see below)
     const bool track = (p >= 2);
     // A^(-1/p): y_0 = e_pos and y <- T y per step; A^(1/p): y_0 = M_0 e_pos and
     // y <- T^(p-1) y, since S^(1/p) e_pos = lambda_bar^(1/p) X^(p-1) M_0 e_pos at the limit
@@ -1082,7 +1107,6 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
       for (int i = tid; i < mp; i += blockDim.x) {
         const double s0 = i < m ? S[pos * m + i] * inv_lam : 0.0;
         yg[i] = a.sign < 0 ? ((i == pos) ? 1.0 : 0.0) : s0;
-        ug[i] = (float)s0;
       }
     }
     __threadfence();             // planes are read next through L2 (cp.async.cg / TMA)
@@ -1099,8 +1123,9 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
       gemm_sync(A, B, C, Y, flags, io, reinterpret_cast<__half*>(sm));
       return true;
     };
-    auto vec_of = [&](const Mat& Mk, double c, double alpha) {
-      return VecTask{Mk.q, plane, LD, Mk.e, m, mp, p, ny, c, alpha, yg, ug, yhg, ylg, myg, tg};
+    auto vec_of = [&](const Mat& Mk, double c, double alpha, bool track_u) {
+      return VecTask{Mk.q, plane, LD, Mk.e, m, mp, p, ny, c, alpha, yg, ug, yhg, ylg, myg, tg,
+                     track_u};
     };
 
     int xc = 0, mi = 0;
@@ -1120,7 +1145,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
       io.c = st.c;
       io.alpha = st.alpha;
       const Mat Mk = B3[mi];
-      const VecTask vt = vec_of(Mk, (double)st.c, (double)st.alpha);
+      const VecTask vt = vec_of(Mk, (double)st.c, (double)st.alpha, false);
       if (track) {
         // the vector step runs with the first product below
       } else if (iters == 0) {
@@ -1188,8 +1213,15 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     const double c = pow(lam, -1.0 / (double)p);               // F = c X
     if (!bad && track) {
       const double c_out = a.sign < 0 ? c : pow(lam, 1.0 / (double)p);
+      // residual vector u = M_K e_pos (row pos of the symmetric M_K = X_K^p M_0, up to the
+      // products' rounding), carried through the last step with y
+      for (int i = tid; i < mp; i += blockDim.x) {
+        float h = 0.f, l = 0.f;
+        if (i < m) load1_df(B3[mi].q, plane, (size_t)pos * LD + i, B3[mi].e, h, l);
+        ug[i] = h + l;
+      }
       __syncthreads();
-      vec_task<0>(vec_of(B3[mi], 1.0 / (double)p, (double)(p + 1)));
+      vec_task<0>(vec_of(B3[mi], 1.0 / (double)p, (double)(p + 1), true));
       // column pos of the result (lambda_bar^(-1/p) X e_pos, or lambda_bar^(1/p) X^(p-1)
       // M_0 e_pos for A^(1/p)) and the residual F^p s_pos - e_pos = u - e_pos of
       // F = lambda_bar^(-1/p) X
