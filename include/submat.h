@@ -93,6 +93,18 @@ typedef struct {
                               (Sec. 4.2), computed from the same iteration as
                               S^(1/p) e_pos = S (S^(-1/p))^(p-1) e_pos; any other value is
                               SUBMAT_EINVAL.  submat_invroot_noalloc is inverse only.     */
+  int32_t grad_deterministic; /* 0 (default): submat_invroot_backward adds each submatrix's
+                              contributions to grad_in with atomic adds (their order, and so
+                              the last bits, vary from call to call); 1: each stored entry
+                              sums its contributions in a fixed order (the contributing rows
+                              j ascending, in waves of at most grad_wave_mib MiB of
+                              per-submatrix gradients), so repeated calls give identical
+                              bits.  Costs device memory for the waves' gradients, nnz int32
+                              and n+1 int64, allocated by the first such backward; any other
+                              value is SUBMAT_EINVAL.                                     */
+  int32_t grad_wave_mib;   /* deterministic backward: largest device buffer of per-
+                              submatrix gradients per wave, in MiB (a wave holds at least
+                              one row); <= 0 selects SUBMAT_GRAD_WAVE_MIB                  */
 } submat_opts;
 
 typedef struct {
@@ -152,6 +164,9 @@ SUBMAT_API submat_status submat_invroot(submat_plan_t plan, const double* vals_i
 SUBMAT_API submat_status submat_invroot_host(submat_plan_t plan, const double* vals_in,
                                              double* vals_out, void* stream);
 
+/* Default largest buffer of per-submatrix gradients of a deterministic backward wave. */
+#define SUBMAT_GRAD_WAVE_MIB 4096
+
 /*
  * Backward (Daleckii-Krein adjoint; Higham, Functions of Matrices, Thm. 3.11, with
  * f(x) = x^(root_sign/p)):
@@ -160,6 +175,9 @@ SUBMAT_API submat_status submat_invroot_host(submat_plan_t plan, const double* v
  * j the submatrix is regathered from the saved vals_in and decomposed again in FP64
  * (recomputation, no stored iterates).  grad_out and grad_in are device arrays of nnz
  * doubles; grad_in is overwritten.  Returns SUBMAT_ENOFWD if no forward ran on this plan.
+ * With opts.grad_deterministic = 1 the per-submatrix gradients G_j of a wave of rows are
+ * stored, and each entry (r, c) then adds G_j(r, c) over the wave's rows j whose patterns
+ * hold both r and c (the transposed map of the plan: j in R_r and R_c), without atomics.
  */
 SUBMAT_API submat_status submat_invroot_backward(submat_plan_t plan, const double* grad_out,
                                       double* grad_in, void* stream);

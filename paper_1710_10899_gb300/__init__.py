@@ -50,7 +50,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("k_max", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("resid_tol", ctypes.c_double),
                 ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("kappa_max", ctypes.c_double), ("root_sign", ctypes.c_int32)]
+                ("kappa_max", ctypes.c_double), ("root_sign", ctypes.c_int32),
+                ("grad_deterministic", ctypes.c_int32), ("grad_wave_mib", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -133,7 +134,8 @@ class Plan:
 
     def __init__(self, rowptr, colind, p: int, precision: str = "mixed", k_max: int = 0,
                  tol: float = 0.0, resid_tol: float = 0.0, refine_steps: int = -1,
-                 use_graph: bool = True, kappa_max: float = 0.0, root_sign: int = -1):
+                 use_graph: bool = True, kappa_max: float = 0.0, root_sign: int = -1,
+                 grad_deterministic: bool = False, grad_wave_mib: int = 0):
         lib = load_library()
         self._lib = lib
         torch = _torch()
@@ -163,6 +165,8 @@ class Plan:
         o.use_graph = 1 if use_graph else 0
         o.kappa_max = kappa_max
         o.root_sign = int(root_sign)
+        o.grad_deterministic = 1 if grad_deterministic else 0
+        o.grad_wave_mib = int(grad_wave_mib)
         h = ctypes.c_void_p()
         _check(lib, lib.submat_plan(ctypes.byref(csr), int(p), ctypes.byref(o), ctypes.byref(h)))
         self._h = h

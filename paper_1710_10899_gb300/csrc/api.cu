@@ -80,6 +80,13 @@ struct submat_plan_s {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   double* d_host_in = nullptr;     // device staging of submat_invroot_host
   double* d_host_out = nullptr;
+  // deterministic backward (allocated by the first one): row sizes, transposed positions,
+  // offsets of the per-row gradients G_j, the waves' buffer and the waves' row ranges
+  std::vector<int32_t> h_m;
+  int32_t* d_tpos = nullptr;
+  int64_t* d_gofs = nullptr;
+  double* d_gbuf = nullptr;
+  std::vector<std::pair<int32_t, int32_t>> waves;
   std::vector<GraphEntry> graphs;
 };
 
@@ -97,6 +104,9 @@ void release(submat_plan_t P) {
     if (e) cudaEventDestroy(e);
   cudaFree(P->d_host_in);
   cudaFree(P->d_host_out);
+  cudaFree(P->d_tpos);
+  cudaFree(P->d_gofs);
+  cudaFree(P->d_gbuf);
   cudaFree(P->d_rowptr);
   cudaFree(P->d_colind);
   cudaFree(P->d_m);
@@ -168,6 +178,8 @@ void submat_default_opts(submat_opts* o) {
   o->use_graph = 1;
   o->kappa_max = 100.0;
   o->root_sign = -1;
+  o->grad_deterministic = 0;
+  o->grad_wave_mib = 0;
 }
 
 const char* submat_status_string(submat_status s) {
@@ -212,6 +224,9 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   if (o.refine_steps < 0) o.refine_steps = (p == 1) ? 2 : 0;
   if (!(o.kappa_max > 0.0)) o.kappa_max = 100.0;
   if (o.root_sign != -1 && o.root_sign != 1) return fail(SUBMAT_EINVAL, "root_sign must be -1 or +1");
+  if (o.grad_deterministic != 0 && o.grad_deterministic != 1)
+    return fail(SUBMAT_EINVAL, "grad_deterministic must be 0 or 1");
+  if (o.grad_wave_mib <= 0) o.grad_wave_mib = SUBMAT_GRAD_WAVE_MIB;
 
   const int32_t n = csr->n;
   const int64_t nnz = csr->nnz;
@@ -309,6 +324,7 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   }
   if (n > 0)
     PLAN_TRY(cudaMemcpy(P->d_order, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+  P->h_m.assign(h_m.begin(), h_m.begin() + n);
 
   const int mp = std::max(pad_mixed(m_max), pad_fp64(m_max));
   const bool mixed = o.precision != SUBMAT_PREC_FP64;
@@ -470,7 +486,41 @@ submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, d
   a.sign = P->opts.root_sign;
   CUDA_TRY(cudaMemsetAsync(grad_in, 0, (size_t)P->nnz * sizeof(double), s));
   CUDA_TRY(cudaMemsetAsync(P->d_ctr_bwd, 0, sizeof(DevCounters), s));
-  CUDA_TRY(launch_backward(a, P->grid, s));
+  if (!P->opts.grad_deterministic) {
+    CUDA_TRY(launch_backward(a, P->grid, s));
+  } else {
+    if (!P->d_tpos) {
+      // transposed positions, G_j offsets and waves of at most grad_wave_mib MiB
+      std::vector<int64_t> gofs(P->n + 1, 0);
+      for (int32_t j = 0; j < P->n; ++j) gofs[j + 1] = gofs[j] + (int64_t)P->h_m[j] * P->h_m[j];
+      const int64_t cap = (int64_t)P->opts.grad_wave_mib * 1024 * 1024 / (int64_t)sizeof(double);
+      P->waves.clear();
+      int64_t wave_max = 0;
+      for (int32_t j0 = 0; j0 < P->n;) {
+        int32_t j1 = j0 + 1;
+        while (j1 < P->n && gofs[j1 + 1] - gofs[j0] <= cap) ++j1;
+        P->waves.emplace_back(j0, j1);
+        wave_max = std::max(wave_max, gofs[j1] - gofs[j0]);
+        j0 = j1;
+      }
+      CUDA_TRY(cudaMalloc(&P->d_gofs, (P->n + 1) * sizeof(int64_t)));
+      CUDA_TRY(cudaMemcpy(P->d_gofs, gofs.data(), (P->n + 1) * sizeof(int64_t),
+                          cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMalloc(&P->d_gbuf, (size_t)wave_max * sizeof(double)));
+      CUDA_TRY(cudaMalloc(&P->d_tpos, (size_t)P->nnz * sizeof(int32_t)));
+      CUDA_TRY(launch_transposed_positions(P->d_rowptr, P->d_colind, P->n, P->d_tpos, s));
+    }
+    a.gbuf = P->d_gbuf;
+    a.gofs = P->d_gofs;
+    for (const auto& w : P->waves) {
+      a.j0 = w.first;
+      a.j1 = w.second;
+      CUDA_TRY(cudaMemsetAsync(&P->d_ctr_bwd->queue, 0, sizeof(int32_t), s));   // job queue
+      CUDA_TRY(launch_backward(a, P->grid, s));
+      CUDA_TRY(launch_grad_gather(P->d_rowptr, P->d_colind, P->d_tpos, P->d_m, P->d_gofs,
+                                  P->d_gbuf, P->n, w.first, w.second, grad_in, s));
+    }
+  }
   P->last_stream = s;
   if (prev != P->device) CUDA_TRY(cudaSetDevice(prev));
   return SUBMAT_OK;

@@ -74,6 +74,12 @@ struct BwdArgs {
   char* scratch;
   size_t scratch_stride;
   int32_t sign;              // -1: A^(-1/p), +1: A^(1/p)
+  // deterministic scatter: when gbuf is set, rows j in [j0, j1) write G_j (m_j x m_j,
+  // row-major) to gbuf + gofs[j] - gofs[j0] instead of adding it into grad_in, and the
+  // other rows are skipped
+  double* gbuf;
+  const int64_t* gofs;       // [n+1] exclusive prefix sums of m_j^2
+  int32_t j0, j1;
 };
 
 // Launchers (return cudaGetLastError() of the launch).
@@ -85,6 +91,16 @@ cudaError_t launch_fwd_mixed(const FwdArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_fwd_fp64(const FwdArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_fallback(const FwdArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_backward(const BwdArgs& a, int grid, cudaStream_t s);
+// Transposed positions of the plan: for the entry e = (r, j) of row r, tpos[e] = the index
+// of r in row j's column list (the position of row r in R_j).
+cudaError_t launch_transposed_positions(const int32_t* rowptr, const int32_t* colind,
+                                        int32_t n, int32_t* tpos, cudaStream_t s);
+// grad_in[e] += sum over j in R_r and R_c, j0 <= j < j1, of G_j(r, c) (e = (r, c)), the
+// G_j stored by a deterministic backward wave; each entry's sum in a fixed order.
+cudaError_t launch_grad_gather(const int32_t* rowptr, const int32_t* colind, const int32_t* tpos,
+                               const int32_t* m, const int64_t* gofs, const double* gbuf,
+                               int32_t n, int32_t j0, int32_t j1, double* grad_in,
+                               cudaStream_t s);
 
 // Dynamic shared memory of each kernel (bytes), for cudaFuncSetAttribute at plan time.
 size_t smem_fwd_mixed();

@@ -12,6 +12,7 @@
 //             added into the gradient of every stored entry (R[k], R[l]).
 //
 // Rotation: the symmetric 2x2 Schur decomposition of Golub & Van Loan (Alg. 8.4.1).
+#include <algorithm>
 #include "common.cuh"
 #include "jacobi.cuh"
 
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
     __syncthreads();
     if (idx >= a.n) break;
     const int j = a.order[idx];
+    if (a.gbuf && (j < a.j0 || j >= a.j1)) continue;     // another wave's row
     const int m = a.m[j], pos = a.pos[j], p = a.p;
     double* A = reinterpret_cast<double*>(scr);
     double* V = A + (size_t)m * m;
@@ -114,6 +116,10 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
     __syncthreads();
     if (bad_s) {
       if (tid == 0) atomicAdd(&a.ctr->n_notspd, 1ull);
+      if (a.gbuf) {              // no contribution, as in the atomic scatter
+        double* gj = a.gbuf + (a.gofs[j] - a.gofs[a.j0]);
+        for (int e = tid; e < m * m; e += blockDim.x) gj[e] = 0.0;
+      }
       __syncthreads();
       continue;
     }
@@ -149,6 +155,13 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
       A[e] = s;
     }
     __syncthreads();
+    if (a.gbuf) {                // deterministic: keep G_j for the gather pass
+      double* gj = a.gbuf + (a.gofs[j] - a.gofs[a.j0]);
+      for (int e = tid; e < m * m; e += blockDim.x) gj[e] = A[e];
+      if (tid == 0) atomicAdd(&a.ctr->flops_fp64, 16.0 * (double)m * m * m);
+      __syncthreads();
+      continue;
+    }
     // scatter-add G[k][l] into the stored entry (R[k], R[l])
     for (int k = warp; k < m; k += nwarps()) {
       const int r = R_s[k];
@@ -162,7 +175,84 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
   }
 }
 
+// tpos[e] for e = (r, j): the index of r in row j's sorted column list.
+__global__ void transposed_positions_kernel(const int32_t* __restrict__ rowptr,
+                                            const int32_t* __restrict__ colind, int32_t n,
+                                            int32_t* __restrict__ tpos) {
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps)
+    for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += 32) {
+      const int j = colind[e];
+      tpos[e] = find_sorted(colind + rowptr[j], rowptr[j + 1] - rowptr[j], r);
+    }
+}
+
+// One CTA per row r (grid-stride), one warp per stored entry (r, c) of it: the rows j of
+// R_c (32 at a time, lanes in ascending order) that also lie in R_r (a bisection in R_r,
+// staged in shared memory) and in [j0, j1) contribute G_j(k, l), k = position of r in R_j,
+// l = position of c in R_j.  Lanes combine by a fixed butterfly and the 32-row chunks in
+// order, so the sum does not depend on timing.
+__global__ void __launch_bounds__(256) grad_gather_kernel(
+    const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+    const int32_t* __restrict__ tpos, const int32_t* __restrict__ mrow,
+    const int64_t* __restrict__ gofs, const double* __restrict__ gbuf, int32_t n, int32_t j0,
+    int32_t j1, double* __restrict__ grad_in) {
+  __shared__ int32_t R_s[SUBMAT_MAX_M];      // R_r
+  __shared__ int32_t K_s[SUBMAT_MAX_M];      // position of r in R_j for each j in R_r
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int64_t base = gofs[j0];
+  for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    const int rb = rowptr[r], mr = rowptr[r + 1] - rb;
+    for (int i = tid; i < mr; i += blockDim.x) {
+      R_s[i] = colind[rb + i];
+      K_s[i] = tpos[rb + i];
+    }
+    __syncthreads();
+    for (int ci = warp; ci < mr; ci += nw) {
+      const int c = R_s[ci], cb = rowptr[c], ce = rowptr[c + 1];
+      double sum = 0.0;
+      for (int q0 = cb; q0 < ce; q0 += 32) {
+        const int q = q0 + lane;
+        double v = 0.0;
+        if (q < ce) {
+          const int j = colind[q];
+          if (j >= j0 && j < j1) {
+            const int idx = find_sorted(R_s, mr, j);
+            if (idx >= 0) {
+              const int mj = mrow[j];
+              v = gbuf[(gofs[j] - base) + (int64_t)K_s[idx] * mj + tpos[q]];
+            }
+          }
+        }
+        sum += warp_sum(v);
+      }
+      if (lane == 0) grad_in[rb + ci] += sum;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_transposed_positions(const int32_t* rowptr, const int32_t* colind,
+                                        int32_t n, int32_t* tpos, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>(((int64_t)n * 32 + 255) / 256, 65535);
+  transposed_positions_kernel<<<blocks, 256, 0, s>>>(rowptr, colind, n, tpos);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_gather(const int32_t* rowptr, const int32_t* colind, const int32_t* tpos,
+                               const int32_t* m, const int64_t* gofs, const double* gbuf,
+                               int32_t n, int32_t j0, int32_t j1, double* grad_in,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = std::min(n, 152 * 8);
+  grad_gather_kernel<<<blocks, 256, 0, s>>>(rowptr, colind, tpos, m, gofs, gbuf, n, j0, j1,
+                                            grad_in);
+  return cudaGetLastError();
+}
 
 size_t smem_fallback() {
   return (2 * SUBMAT_MAX_M + kRedDoubles) * sizeof(double) + 2 * SUBMAT_MAX_M * sizeof(int32_t);

@@ -44,6 +44,7 @@ def test_status_strings_and_defaults(lib):
     lib.submat_default_opts(ctypes.byref(o))
     assert o.precision == pkg.PREC_MIXED_F16 and o.k_max == 40 and o.use_graph == 1
     assert o.root_sign == -1 and o.kappa_max == 100.0
+    assert o.grad_deterministic == 0 and o.grad_wave_mib == 0
 
 
 def _plan_status(lib, rowptr, colind, p=2):
@@ -74,6 +75,10 @@ def test_host_side_validation(lib):
     ci = np.array([0], dtype=np.int32)
     csr = pkg.CSR(1, 1, rp.ctypes.data, ci.ctypes.data, 0)
     h = ctypes.c_void_p()
+    assert pkg.STATUS[lib.submat_plan(ctypes.byref(csr), 2, ctypes.byref(o), ctypes.byref(h))] == "SUBMAT_EINVAL"
+    # grad_deterministic other than 0 / 1
+    lib.submat_default_opts(ctypes.byref(o))
+    o.grad_deterministic = 2
     assert pkg.STATUS[lib.submat_plan(ctypes.byref(csr), 2, ctypes.byref(o), ctypes.byref(h))] == "SUBMAT_EINVAL"
 
 
