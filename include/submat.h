@@ -182,6 +182,24 @@ SUBMAT_API submat_status submat_invroot_host(submat_plan_t plan, const double* v
 SUBMAT_API submat_status submat_invroot_backward(submat_plan_t plan, const double* grad_out,
                                       double* grad_in, void* stream);
 
+/*
+ * Conjugate gradients on A x = b for A on the plan's pattern (Sec. 4.4, the submatrix
+ * method as a preconditioner).  vals_a: A's values (device, nnz doubles, SPD); b, x:
+ * device arrays of n doubles (x is overwritten; it starts from zero).  With vals_k == NULL
+ * plain CG; otherwise K (values vals_k on the same pattern, CSR, e.g. the result of
+ * submat_invroot with p = 2, K ~ A^(-1/2)) is applied as in Sec. 4.4: CG on
+ * K^T A K y = K^T b, then x = K y.  Stops when the 2-norm of the iterated system's residual
+ * is at most tol (<= 0: 1e-6) times that of its right-hand side, or after max_iter
+ * (<= 0: 2n) steps; *iters and *rel_resid (either may be NULL) receive the step count and
+ * that final ratio.  Dot products are reduced in a fixed order, so repeated calls give the
+ * same bits.  Synchronous on the stream.  Work vectors (6n + nnz doubles) are allocated by
+ * the plan's first call.  Returns SUBMAT_ENOTSPD if p^T A p <= 0 occurs (x then holds the
+ * last iterate, mapped by K when given).
+ */
+SUBMAT_API submat_status submat_pcg(submat_plan_t plan, const double* vals_a, const double* vals_k,
+                                    const double* b, double* x, double tol, int32_t max_iter,
+                                    int32_t* iters, double* rel_resid, void* stream);
+
 /* Counters of the last forward (synchronises the plan's stream). */
 SUBMAT_API submat_status submat_get_report(submat_plan_t plan, submat_report* out);
 

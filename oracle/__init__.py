@@ -7,3 +7,4 @@ from .submatrix import (  # noqa: F401
     index_set, plan, submatrix, inv_root, inv_root_column, invroot, row_segment,
     divided_differences, submatrix_grad, grad, to_dense, residual_2norm,
 )
+from . import cg  # noqa: F401,E402

@@ -70,7 +70,7 @@ class Report(ctypes.Structure):
 EXPORTS = ["submat_default_opts", "submat_plan", "submat_invroot", "submat_invroot_host",
            "submat_invroot_backward",
            "submat_get_report", "submat_plan_rows", "submat_plan_shape", "submat_plan_destroy",
-           "submat_status_string", "submat_last_error", "submat_invroot_noalloc"]
+           "submat_status_string", "submat_last_error", "submat_invroot_noalloc", "submat_pcg"]
 
 _lib_handle = None
 
@@ -108,6 +108,9 @@ def load_library(path: str = LIB_PATH):
     lib.submat_last_error.restype = ctypes.c_char_p
     lib.submat_invroot_noalloc.argtypes = [i32, ctypes.c_int64, vp, vp, i32, i32, vp, vp, vp]
     lib.submat_invroot_noalloc.restype = i32
+    lib.submat_pcg.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, i32, ctypes.POINTER(i32),
+                               ctypes.POINTER(ctypes.c_double), vp]
+    lib.submat_pcg.restype = i32
     _lib_handle = lib
     return lib
 
@@ -255,6 +258,31 @@ def submat_invroot(plan: Plan, vals_in, vals_out=None, stream=None, sync: bool =
 def submat_invroot_backward(plan: Plan, grad_out, grad_in=None, stream=None):
     """``submat_invroot_backward``: gradient w.r.t. A's stored values (last forward)."""
     return plan.backward(grad_out, grad_in, stream)
+
+
+def submat_pcg(plan: Plan, vals_a, b=None, vals_k=None, tol: float = 1e-6, max_iter: int = 0,
+               stream=None):
+    """``submat_pcg``: conjugate gradients on A x = b (b defaults to ones) for A on the
+    plan's pattern, plain or, with ``vals_k`` (e.g. the p = 2 result of ``submat_invroot``,
+    K ~ A^(-1/2)), on K^T A K y = K^T b with x = K y (Sec. 4.4).  Returns
+    (x, iterations, relative residual of the iterated system)."""
+    torch = _torch()
+    va = plan._vals(vals_a)
+    if b is None:
+        b = torch.ones(plan.n, dtype=torch.float64, device=va.device)
+    b = b.to(device=va.device, dtype=torch.float64).contiguous()
+    if b.numel() != plan.n:
+        raise ValueError(f"expected {plan.n} right-hand side values, got {b.numel()}")
+    vk = plan._vals(vals_k) if vals_k is not None else None
+    x = torch.empty_like(b)
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    _check(plan._lib, plan._lib.submat_pcg(
+        plan._h, ctypes.c_void_p(va.data_ptr()),
+        ctypes.c_void_p(vk.data_ptr()) if vk is not None else None,
+        ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), float(tol), int(max_iter),
+        ctypes.byref(it), ctypes.byref(rel), _stream_ptr(stream)))
+    return x, int(it.value), float(rel.value)
 
 
 SUBMAT_NOALLOC_MAX_M = 1024

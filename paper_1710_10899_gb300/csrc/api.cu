@@ -87,6 +87,7 @@ struct submat_plan_s {
   int64_t* d_gofs = nullptr;
   double* d_gbuf = nullptr;
   std::vector<std::pair<int32_t, int32_t>> waves;
+  double* d_cg = nullptr;          // submat_pcg work vectors (allocated by the first call)
   std::vector<GraphEntry> graphs;
 };
 
@@ -107,6 +108,7 @@ void release(submat_plan_t P) {
   cudaFree(P->d_tpos);
   cudaFree(P->d_gofs);
   cudaFree(P->d_gbuf);
+  cudaFree(P->d_cg);
   cudaFree(P->d_rowptr);
   cudaFree(P->d_colind);
   cudaFree(P->d_m);
@@ -120,6 +122,15 @@ void release(submat_plan_t P) {
   cudaFree(P->d_saved);
   cudaSetDevice(prev);
   delete P;
+}
+
+// The plan's transposed map (computed once): tpos[e] for e = (r, j) is the position of r in
+// row j's column list.
+cudaError_t ensure_tpos(submat_plan_t P, cudaStream_t s) {
+  if (P->d_tpos || P->nnz == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&P->d_tpos, (size_t)P->nnz * sizeof(int32_t));
+  if (e != cudaSuccess) return e;
+  return launch_transposed_positions(P->d_rowptr, P->d_colind, P->n, P->d_tpos, s);
 }
 
 // Queue the forward of plan P on stream s.
@@ -489,8 +500,10 @@ submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, d
   if (!P->opts.grad_deterministic) {
     CUDA_TRY(launch_backward(a, P->grid, s));
   } else {
-    if (!P->d_tpos) {
-      // transposed positions, G_j offsets and waves of at most grad_wave_mib MiB
+    if (!P->d_gbuf) {
+      // G_j offsets and waves of at most grad_wave_mib MiB
+      cudaFree(P->d_gofs);                     // left by an earlier call that ran out of memory
+      P->d_gofs = nullptr;
       std::vector<int64_t> gofs(P->n + 1, 0);
       for (int32_t j = 0; j < P->n; ++j) gofs[j + 1] = gofs[j] + (int64_t)P->h_m[j] * P->h_m[j];
       const int64_t cap = (int64_t)P->opts.grad_wave_mib * 1024 * 1024 / (int64_t)sizeof(double);
@@ -507,9 +520,8 @@ submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, d
       CUDA_TRY(cudaMemcpy(P->d_gofs, gofs.data(), (P->n + 1) * sizeof(int64_t),
                           cudaMemcpyHostToDevice));
       CUDA_TRY(cudaMalloc(&P->d_gbuf, (size_t)wave_max * sizeof(double)));
-      CUDA_TRY(cudaMalloc(&P->d_tpos, (size_t)P->nnz * sizeof(int32_t)));
-      CUDA_TRY(launch_transposed_positions(P->d_rowptr, P->d_colind, P->n, P->d_tpos, s));
     }
+    CUDA_TRY(ensure_tpos(P, s));
     a.gbuf = P->d_gbuf;
     a.gofs = P->d_gofs;
     for (const auto& w : P->waves) {
@@ -524,6 +536,88 @@ submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, d
   P->last_stream = s;
   if (prev != P->device) CUDA_TRY(cudaSetDevice(prev));
   return SUBMAT_OK;
+}
+
+submat_status submat_pcg(submat_plan_t P, const double* vals_a, const double* vals_k,
+                         const double* b, double* x, double tol, int32_t max_iter,
+                         int32_t* iters, double* rel_resid, void* stream) {
+  g_last_error.clear();
+  if (!P) return fail(SUBMAT_EINVAL, "plan is NULL");
+  if (!vals_a || !b || !x) return fail(SUBMAT_EINVAL, "NULL array");
+  if (iters) *iters = 0;
+  if (rel_resid) *rel_resid = 0.0;
+  if (P->n == 0) return SUBMAT_OK;
+  if (!(tol > 0.0)) tol = 1e-6;
+  if (max_iter <= 0) max_iter = 2 * P->n;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int prev = 0;
+  CUDA_TRY(cudaGetDevice(&prev));
+  if (prev != P->device) CUDA_TRY(cudaSetDevice(P->device));
+  const int32_t n = P->n;
+  const size_t nd = (size_t)n;
+  if (!P->d_cg) {
+    const size_t words = 6 * nd + (size_t)P->nnz + cg_dot_scratch() + 2;
+    CUDA_TRY(cudaMalloc(&P->d_cg, words * sizeof(double)));
+  }
+  double* r = P->d_cg;
+  double* p = r + nd;
+  double* q = p + nd;
+  double* t1 = q + nd;
+  double* t2 = t1 + nd;
+  double* y = t2 + nd;                      // the iterate (x itself without K)
+  double* kt = y + nd;                      // K^T's values
+  double* part = kt + P->nnz;
+  double* scal = part + cg_dot_scratch();
+  const bool pre = vals_k != nullptr;
+  double* it_x = pre ? y : x;
+  if (pre) {
+    CUDA_TRY(ensure_tpos(P, s));
+    CUDA_TRY(cg_transpose_vals(P->d_rowptr, P->d_colind, P->d_tpos, vals_k, kt, P->nnz, s));
+    CUDA_TRY(cg_spmv(P->d_rowptr, P->d_colind, kt, b, r, n, s));          // r = K^T b
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(r, b, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  CUDA_TRY(cudaMemsetAsync(it_x, 0, nd * sizeof(double), s));
+  CUDA_TRY(cudaMemcpyAsync(p, r, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cg_dot(r, r, n, part, scal, s));
+  double rr = 0.0;
+  CUDA_TRY(cudaMemcpyAsync(&rr, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(rr);
+  int32_t it = 0;
+  submat_status st = SUBMAT_OK;
+  while (bnorm > 0.0 && std::sqrt(rr) > tol * bnorm && it < max_iter) {
+    if (pre) {                                                            // q = K^T A K p
+      CUDA_TRY(cg_spmv(P->d_rowptr, P->d_colind, vals_k, p, t1, n, s));
+      CUDA_TRY(cg_spmv(P->d_rowptr, P->d_colind, vals_a, t1, t2, n, s));
+      CUDA_TRY(cg_spmv(P->d_rowptr, P->d_colind, kt, t2, q, n, s));
+    } else {                                                              // q = A p
+      CUDA_TRY(cg_spmv(P->d_rowptr, P->d_colind, vals_a, p, q, n, s));
+    }
+    CUDA_TRY(cg_dot(p, q, n, part, scal, s));
+    double pq = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(&pq, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (!(pq > 0.0) || !std::isfinite(pq)) {      // the operator is not positive definite
+      st = fail(SUBMAT_ENOTSPD, "CG: p^T A p <= 0");
+      break;
+    }
+    const double alpha = rr / pq;
+    CUDA_TRY(cg_update(alpha, it_x, r, p, q, n, part, scal + 1, s));
+    double rr_new = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(&rr_new, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cg_dir(rr_new / rr, r, p, n, s));
+    rr = rr_new;
+    ++it;
+  }
+  if (pre) CUDA_TRY(cg_spmv(P->d_rowptr, P->d_colind, vals_k, y, x, n, s));   // x = K y
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (iters) *iters = it;
+  if (rel_resid) *rel_resid = bnorm > 0.0 ? std::sqrt(rr) / bnorm : 0.0;
+  P->last_stream = s;
+  if (prev != P->device) CUDA_TRY(cudaSetDevice(prev));
+  return st;
 }
 
 submat_status submat_get_report(submat_plan_t P, submat_report* r) {

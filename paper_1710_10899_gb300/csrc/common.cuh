@@ -102,6 +102,19 @@ cudaError_t launch_grad_gather(const int32_t* rowptr, const int32_t* colind, con
                                int32_t n, int32_t j0, int32_t j1, double* grad_in,
                                cudaStream_t s);
 
+// Conjugate-gradient pieces (cg.cu).  cg_dot / cg_update reduce in a fixed order through
+// cg_dot_scratch() doubles of part.
+cudaError_t cg_spmv(const int32_t* rowptr, const int32_t* colind, const double* vals,
+                    const double* x, double* y, int32_t n, cudaStream_t s);
+cudaError_t cg_transpose_vals(const int32_t* rowptr, const int32_t* colind, const int32_t* tpos,
+                              const double* vals, double* kt, int64_t nnz, cudaStream_t s);
+cudaError_t cg_dot(const double* x, const double* y, int32_t n, double* part, double* out,
+                   cudaStream_t s);
+cudaError_t cg_update(double alpha, double* x, double* r, const double* p, const double* q,
+                      int32_t n, double* part, double* rr, cudaStream_t s);
+cudaError_t cg_dir(double beta, const double* r, double* p, int32_t n, cudaStream_t s);
+size_t cg_dot_scratch();
+
 // Dynamic shared memory of each kernel (bytes), for cudaFuncSetAttribute at plan time.
 size_t smem_fwd_mixed();
 size_t smem_fwd_fp64();

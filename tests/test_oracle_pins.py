@@ -338,3 +338,57 @@ def test_positive_root_grad_frechet_and_central_differences(p):
     d /= np.linalg.norm(d)
     fd = (loss(a.vals + h * d) - loss(a.vals - h * d)) / (2 * h)
     assert abs(fd - gr @ d) <= 1e-6 * max(1.0, abs(fd))
+
+
+# --- the preconditioning application (Sec. 4.4): CG oracle pins ---------------------------
+def _dense_csr(a):
+    n = a.shape[0]
+    return (np.arange(0, n * n + 1, n, dtype=np.int32), np.tile(np.arange(n, dtype=np.int32), n),
+            a.ravel().astype(np.float64))
+
+
+def test_cg_products_brute_force():
+    """spmv / spmv_t against dense products on a random (value-nonsymmetric) sparse matrix."""
+    a = wl.random_sparse_spd(40, 0.2, seed=3)
+    v = wl.random_on_pattern(a, seed=5)
+    dense = oracle.to_dense(a.n, a.rowptr, a.colind, v)
+    x = np.random.default_rng(1).standard_normal(a.n)
+    np.testing.assert_allclose(oracle.cg.spmv(a.rowptr, a.colind, v, x), dense @ x, atol=1e-12)
+    np.testing.assert_allclose(oracle.cg.spmv_t(a.rowptr, a.colind, v, x), dense.T @ x, atol=1e-12)
+
+
+def test_cg_terminates_after_distinct_eigenvalues():
+    """In exact arithmetic CG ends after as many steps as A has distinct eigenvalues (with
+    b touching all of them); on a diagonal with three values it takes three."""
+    d = np.array([1.0, 2.0, 5.0] * 4)
+    n = d.shape[0]
+    rp, ci = np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32)
+    x, it, rel, true = oracle.cg.solve(rp, ci, d, np.ones(n), tol=1e-12)
+    assert it == 3 and rel <= 1e-12
+    np.testing.assert_allclose(x, 1.0 / d, rtol=1e-12)
+
+
+def test_cg_matches_dense_solve():
+    rng = np.random.default_rng(7)
+    b_ = rng.standard_normal((30, 30))
+    a = b_ @ b_.T + 30 * np.eye(30)
+    rp, ci, v = _dense_csr(a)
+    b = rng.standard_normal(30)
+    x, it, rel, true = oracle.cg.solve(rp, ci, v, b, tol=1e-13)
+    np.testing.assert_allclose(x, np.linalg.solve(a, b), rtol=1e-10, atol=1e-12)
+    assert true <= 1e-12
+
+
+def test_pcg_with_exact_inverse_square_root_takes_one_step():
+    """On a dense pattern the submatrix method is exact (every submatrix is A), so
+    K = A^(-1/2), K^T A K = I and CG on the transformed system ends after one step with
+    x = K K^T b = A^(-1) b."""
+    rng = np.random.default_rng(11)
+    b_ = rng.standard_normal((20, 20))
+    a = b_ @ b_.T + 5 * np.eye(20)
+    rp, ci, v = _dense_csr(a)
+    k = oracle.invroot(rp, ci, v, 2)
+    b = np.ones(20)
+    x, it, rel, true = oracle.cg.solve(rp, ci, v, b, vals_k=k, tol=1e-10)
+    assert it == 1 and true <= 1e-10
+    np.testing.assert_allclose(x, np.linalg.solve(a, b), rtol=1e-9)

@@ -27,6 +27,10 @@ Recipes (numpy PCG64, seed 0 unless stated):
   block entries are the overlaps of normalised Gaussians with exponents geometric in
   0.5 .. 8 r_c^-2, (2 sqrt(a b) / (a + b))^(3/2) exp(-a b / (a + b) r^2); diagonal shift
   to kappa ~ 1e4.  Submatrix orders are 13 x (number of neighbour atoms), ~845 on average.
+* ``laplace2d_aniso``, ``jump3d`` (inputs of the preconditioning experiment, Sec. 4.4, whose
+  SuiteSparse matrices are not available): an anisotropic 2-D 5-point Laplacian (64^2,
+  coupling 1 / 0.01) and a 3-D 7-point operator with block-wise coefficients spanning four
+  decades (16^3); both SPD, n = 4096.
 
 Every generator can also be scaled down (``n=``) for fast tests; the box side is then
 rescaled so the expected number of neighbours stays the same.
@@ -232,10 +236,82 @@ def block_overlap(atoms: int = 20000, funcs: int = 13, seed: int = 0,
                g.data.astype(np.float64), f"block_overlap(atoms={atoms},funcs={funcs},kappa={kappa:g})")
 
 
+def _stencil_csr(offdiag: dict, diag: np.ndarray, name: str) -> CSR:
+    """CSR of a symmetric matrix from its off-diagonal pairs {(i, j): v} (i < j) and its
+    diagonal."""
+    n = diag.shape[0]
+    if offdiag:
+        ij = np.array(list(offdiag.keys()), dtype=np.int64)
+        v = np.array(list(offdiag.values()), dtype=np.float64)
+    else:
+        ij = np.zeros((0, 2), dtype=np.int64)
+        v = np.zeros(0)
+    return _from_pairs_diag(n, ij, v, diag, name)
+
+
+def _from_pairs_diag(n, pairs, offvals, diag, name) -> CSR:
+    i = np.concatenate([pairs[:, 0], pairs[:, 1], np.arange(n)])
+    j = np.concatenate([pairs[:, 1], pairs[:, 0], np.arange(n)])
+    v = np.concatenate([offvals, offvals, diag])
+    m = sp.csr_matrix((v, (i, j)), shape=(n, n))
+    m.sum_duplicates()
+    m.sort_indices()
+    return CSR(n, m.indptr.astype(np.int32), m.indices.astype(np.int32),
+               m.data.astype(np.float64), name)
+
+
+def laplace2d_aniso(nx: int = 64, eps: float = 0.01) -> CSR:
+    """Stand-in for the SuiteSparse SPD matrices of the preconditioning experiment
+    (Sec. 4.4, 1000 <= n <= 5000, not available here): the 5-point Dirichlet Laplacian on an
+    nx x nx grid with coupling 1 along x and eps along y (n = nx^2; condition number
+    ~ 4 / ((1 + eps) (pi / (nx + 1))^2), ~1.7e3 at the defaults)."""
+    n = nx * nx
+    off = {}
+    diag = np.zeros(n)
+    for y in range(nx):
+        for x in range(nx):
+            k = y * nx + x
+            diag[k] = 2.0 + 2.0 * eps
+            if x + 1 < nx:
+                off[(k, k + 1)] = -1.0
+            if y + 1 < nx:
+                off[(k, k + nx)] = -eps
+    return _stencil_csr(off, diag, f"laplace2d_aniso(nx={nx},eps={eps:g})")
+
+
+def jump3d(nx: int = 16, contrast: float = 1e4, seed: int = 0) -> CSR:
+    """Second stand-in for Sec. 4.4: the 7-point finite-volume operator of -div(c grad u)
+    on an nx^3 grid (Dirichlet), with c piecewise constant on 4^3-cell blocks, each block's
+    c = contrast^u, u ~ U[0,1] (numpy PCG64, seed); face coefficients are harmonic means.
+    n = nx^3 (4096 at the defaults)."""
+    rng = np.random.default_rng(seed)
+    nb = (nx + 3) // 4
+    cb = contrast ** rng.random((nb, nb, nb))
+    c = cb[np.arange(nx)[:, None, None] // 4, np.arange(nx)[None, :, None] // 4,
+           np.arange(nx)[None, None, :] // 4]
+    n = nx ** 3
+    idx = np.arange(n).reshape(nx, nx, nx)
+    off = {}
+    diag = np.zeros(n)
+    for axis in range(3):
+        a = np.moveaxis(c, axis, 0)
+        ia = np.moveaxis(idx, axis, 0)
+        h = 2.0 * a[:-1] * a[1:] / (a[:-1] + a[1:])           # interior faces
+        for k0, k1, w in zip(ia[:-1].ravel(), ia[1:].ravel(), h.ravel()):
+            off[(int(min(k0, k1)), int(max(k0, k1)))] = -float(w)
+            diag[k0] += w
+            diag[k1] += w
+        diag[ia[0].ravel()] += 2.0 * a[0].ravel()            # Dirichlet boundary faces
+        diag[ia[-1].ravel()] += 2.0 * a[-1].ravel()
+    return _stencil_csr(off, diag, f"jump3d(nx={nx},contrast={contrast:g},seed={seed})")
+
+
 WORKLOADS = {
     "overlap_small": overlap_small,
     "overlap_uniform": overlap_uniform,
     "overlap_clustered": overlap_clustered,
     "overlap_grad": overlap_grad,
     "block_overlap": block_overlap,
+    "laplace2d_aniso": laplace2d_aniso,
+    "jump3d": jump3d,
 }
