@@ -9,8 +9,10 @@ mixed precision.  Prints one JSON line.
                     [--workload overlap_uniform|overlap_small|overlap_clustered|overlap_grad]
                     [--p P] [--precision mixed|fp64] [--no-fp64-compare]
 
-With N > 1 (torchrun) the rows are sharded across ranks: each rank plans and computes its
-own share of rows of the same matrix (no data-path collective; weak scaling).
+With N > 1 (torchrun) the workload is built N times larger (same recipe, n x N rows) and
+its rows are sharded across ranks (Sec. 6.1.1: every rank holds the whole matrix and
+computes a contiguous, cost-balanced range of rows; no data-path collective), so the work
+per GPU stays that of the 1-GPU workload (weak scaling).
 """
 from __future__ import annotations
 
@@ -121,15 +123,21 @@ def time_oracle(a, p, seconds, seed=3):
 
 
 # ----------------------------------------------------------------------------------------
-def make_workload(name, p, n=0):
+def make_workload(name, p, n=0, scale=1):
+    """The named workload with n rows (0: its default size), n x scale rows in all."""
+    import inspect
     import workloads as wl
     if name not in wl.WORKLOADS:
         raise SystemExit(f"unknown workload {name}")
-    if n <= 0:
-        return wl.WORKLOADS[name]()
+    fn = wl.WORKLOADS[name]
     if name == "block_overlap":                     # n rows = 13 functions per atom
-        return wl.block_overlap(atoms=max(1, n // 13))
-    return wl.WORKLOADS[name](n=n)
+        atoms = n // 13 if n > 0 else inspect.signature(fn).parameters["atoms"].default
+        return wl.block_overlap(atoms=max(1, atoms * scale))
+    if n <= 0 and scale == 1:
+        return fn()
+    if n <= 0:
+        n = inspect.signature(fn).parameters["n"].default
+    return fn(n=n * scale)
 
 
 def clocks_start():
@@ -206,7 +214,7 @@ def main():
     import numpy as np
 
     log(f"generating {args.workload}")
-    a = make_workload(args.workload, args.p, args.n)
+    a = make_workload(args.workload, args.p, args.n, scale=world)
     p = args.p
     log(f"n={a.n} nnz={a.nnz}")
     workload_name = f"{args.workload}(n={a.n},nnz={a.nnz},p={p})"
@@ -234,8 +242,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    # rows of this rank: contiguous shard of a cost-balanced order (weak scaling: the same
-    # matrix on every rank, each rank computes n/world rows; with world == 1 all rows)
+    # rows of this rank: a contiguous, cost-balanced shard of the world-times-larger matrix
+    # (weak scaling: about the 1-GPU workload's rows per rank; with world == 1 all rows)
     cpu_base = None
     if rank == 0 and world == 1:
         # time the oracle before any GPU work starts the CUDA context in the pool's parent
@@ -244,7 +252,8 @@ def main():
         log(f"oracle: {cpu_base[0]:.1f} rows/s on {cpu_base[1]} cores")
 
     log("plan")
-    plan = sm.submat_plan(a.rowptr, a.colind, p, precision=args.precision)
+    plan = sm.submat_plan(a.rowptr, a.colind, p, precision=args.precision, shard=(rank, world))
+    row_b, row_e = sm.shard_rows(a.rowptr, world, rank)
     log("warm-up")
     vals = torch.tensor(a.vals, device=dev)
     out = torch.empty_like(vals)
@@ -283,7 +292,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    rows_total = a.n * world
+    rows_total = a.n                               # all shards together
     value = rows_total / (ms_per_step / 1e3)
 
     log(f"timed: {ms_per_step:.2f} ms/step")
@@ -293,7 +302,7 @@ def main():
     if rank == 0:
         import oracle
         rng = np.random.default_rng(11)
-        rows = rng.choice(a.n, size=min(48, a.n), replace=False)
+        rows = row_b + rng.choice(row_e - row_b, size=min(48, row_e - row_b), replace=False)
         errs = []
         for j in rows:
             s = slice(a.rowptr[j], a.rowptr[j + 1])
@@ -322,7 +331,7 @@ def main():
     log(f"e2e: {e2e_step:.2f} ms/step")
     # ---- the all-FP64 GPU path on the same input (one step, for the comparison) ----------
     fp64 = None
-    if rank == 0 and not args.no_fp64_compare and args.precision == "mixed":
+    if world == 1 and not args.no_fp64_compare and args.precision == "mixed":
         log("FP64 path (one step)")
         pl64 = sm.submat_plan(a.rowptr, a.colind, p, precision="fp64")
         o64 = torch.empty_like(vals)
@@ -348,6 +357,12 @@ def main():
                 "speedup_mixed_over_fp64": ms64 / ms_per_step}
         del pl64
 
+    if world > 1:                                   # the job's tensor flops (all shards)
+        t = torch.tensor([flops_t], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        flops_job = float(t.item())
+    else:
+        flops_job = flops_t
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -376,13 +391,15 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload_name, "precision": args.precision,
                    "l2": "flushed before every step (512 MB write, untimed)",
-                   "parallelism": f"rows sharded over {world} GPU(s)" if world > 1 else "1 GPU"},
-        "tflops": (flops_per_launch / (ms_per_step / 1e3)) / 1e12,
+                   "parallelism": (f"rows sharded over {world} GPUs (cost-balanced contiguous "
+                                   f"ranges, whole matrix on every GPU)") if world > 1 else "1 GPU"},
+        "tflops": (flops_job / args.steps / (ms_per_step / 1e3)) / 1e12,
         "max_row_rel_err_vs_oracle_sampled": max_err,
         "fallback_rows_per_step": fallbacks / args.steps,
         "roofline": roof,
         "e2e": {"value": rows_total / (e2e_step / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": int(a.nnz * 8), "d2h_bytes_per_step": int(a.nnz * 8)},
+                "h2d_bytes_per_step": int(a.nnz * 8 * world),
+                "d2h_bytes_per_step": int(a.nnz * 8 * world)},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
     }

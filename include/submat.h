@@ -105,6 +105,13 @@ typedef struct {
   int32_t grad_wave_mib;   /* deterministic backward: largest device buffer of per-
                               submatrix gradients per wave, in MiB (a wave holds at least
                               one row); <= 0 selects SUBMAT_GRAD_WAVE_MIB                  */
+  int32_t shard_count;     /* 0 or 1 (default): the plan computes every row; k > 1: only
+                              the rows of shard shard_rank of k (submat_shard_rows), for one
+                              GPU of k each given the whole matrix (Sec. 6.1.1): the forward
+                              writes only those rows' segments of vals_out, the backward
+                              gives those rows' contribution to grad_in (the shards'
+                              grad_in add up to the full gradient)                         */
+  int32_t shard_rank;      /* 0 .. shard_count-1                                          */
 } submat_opts;
 
 typedef struct {
@@ -127,6 +134,17 @@ typedef struct {
 } submat_report;
 
 typedef struct submat_plan_s* submat_plan_t;
+
+/*
+ * Row range [*row_begin, *row_end) of shard rank of count (host call; no GPU needed).
+ * Every worker holds the whole matrix and takes a contiguous range of rows, as in
+ * Sec. 6.1.1, with the boundaries at the quantiles of the rows' cost m_j^3 instead of equal
+ * row counts (the load imbalance Sec. 6.1.3 describes): shard k starts at the first row
+ * whose cumulative cost reaches k/count of the total.  rowptr: host array of n+1 entries.
+ * SUBMAT_EINVAL for count < 1, rank outside [0, count) or NULL pointers.
+ */
+SUBMAT_API submat_status submat_shard_rows(int32_t n, const int32_t* rowptr, int32_t count,
+                                           int32_t rank, int32_t* row_begin, int32_t* row_end);
 
 /* Fill *opts with the defaults. */
 SUBMAT_API void submat_default_opts(submat_opts* opts);

@@ -51,7 +51,8 @@ class Opts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("resid_tol", ctypes.c_double),
                 ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("kappa_max", ctypes.c_double), ("root_sign", ctypes.c_int32),
-                ("grad_deterministic", ctypes.c_int32), ("grad_wave_mib", ctypes.c_int32)]
+                ("grad_deterministic", ctypes.c_int32), ("grad_wave_mib", ctypes.c_int32),
+                ("shard_count", ctypes.c_int32), ("shard_rank", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -70,7 +71,8 @@ class Report(ctypes.Structure):
 EXPORTS = ["submat_default_opts", "submat_plan", "submat_invroot", "submat_invroot_host",
            "submat_invroot_backward",
            "submat_get_report", "submat_plan_rows", "submat_plan_shape", "submat_plan_destroy",
-           "submat_status_string", "submat_last_error", "submat_invroot_noalloc", "submat_pcg"]
+           "submat_status_string", "submat_last_error", "submat_invroot_noalloc", "submat_pcg",
+           "submat_shard_rows"]
 
 _lib_handle = None
 
@@ -111,6 +113,8 @@ def load_library(path: str = LIB_PATH):
     lib.submat_pcg.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, i32, ctypes.POINTER(i32),
                                ctypes.POINTER(ctypes.c_double), vp]
     lib.submat_pcg.restype = i32
+    lib.submat_shard_rows.argtypes = [i32, vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.submat_shard_rows.restype = i32
     _lib_handle = lib
     return lib
 
@@ -138,7 +142,7 @@ class Plan:
     def __init__(self, rowptr, colind, p: int, precision: str = "mixed", k_max: int = 0,
                  tol: float = 0.0, resid_tol: float = 0.0, refine_steps: int = -1,
                  use_graph: bool = True, kappa_max: float = 0.0, root_sign: int = -1,
-                 grad_deterministic: bool = False, grad_wave_mib: int = 0):
+                 grad_deterministic: bool = False, grad_wave_mib: int = 0, shard=(0, 1)):
         lib = load_library()
         self._lib = lib
         torch = _torch()
@@ -170,6 +174,7 @@ class Plan:
         o.root_sign = int(root_sign)
         o.grad_deterministic = 1 if grad_deterministic else 0
         o.grad_wave_mib = int(grad_wave_mib)
+        o.shard_rank, o.shard_count = int(shard[0]), int(shard[1])
         h = ctypes.c_void_p()
         _check(lib, lib.submat_plan(ctypes.byref(csr), int(p), ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -283,6 +288,17 @@ def submat_pcg(plan: Plan, vals_a, b=None, vals_k=None, tol: float = 1e-6, max_i
         ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), float(tol), int(max_iter),
         ctypes.byref(it), ctypes.byref(rel), _stream_ptr(stream)))
     return x, int(it.value), float(rel.value)
+
+
+def shard_rows(rowptr, count: int, rank: int):
+    """``submat_shard_rows``: the contiguous, cost-balanced row range (begin, end) of shard
+    ``rank`` of ``count`` (host computation; works without a GPU)."""
+    lib = load_library()
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    b, e = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib, lib.submat_shard_rows(int(rp.shape[0] - 1), rp.ctypes.data, int(count), int(rank),
+                                      ctypes.byref(b), ctypes.byref(e)))
+    return int(b.value), int(e.value)
 
 
 SUBMAT_NOALLOC_MAX_M = 1024

@@ -54,6 +54,8 @@ struct submat_plan_s {
   int device = 0;
   int n_sm = 0;
   int32_t n = 0;
+  int32_t row_begin = 0, row_end = 0;   // rows this plan computes (its shard; all by default)
+  int32_t n_jobs = 0;                   // row_end - row_begin
   int64_t nnz = 0;
   int32_t p = 1;
   submat_opts opts{};
@@ -143,7 +145,7 @@ submat_status enqueue_forward(submat_plan_t P, const double* in, double* out, cu
   a.m = P->d_m;
   a.pos = P->d_pos;
   a.order = P->d_order;
-  a.n = P->n;
+  a.n = P->n_jobs;                      // rows of this plan (d_order holds them)
   a.p = P->p;
   a.vals_in = in;
   a.vals_out = out;
@@ -179,6 +181,35 @@ submat_status enqueue_forward(submat_plan_t P, const double* in, double* out, cu
 
 extern "C" {
 
+submat_status submat_shard_rows(int32_t n, const int32_t* rowptr, int32_t count, int32_t rank,
+                               int32_t* row_begin, int32_t* row_end) {
+  g_last_error.clear();
+  if (!rowptr || !row_begin || !row_end || n < 0) return fail(SUBMAT_EINVAL, "bad argument");
+  if (count < 1 || rank < 0 || rank >= count)
+    return fail(SUBMAT_EINVAL, "shard rank must lie in [0, count)");
+  // cumulative cost of the rows (m_j^3) and the first row reaching each quantile
+  double total = 0.0;
+  for (int32_t j = 0; j < n; ++j) {
+    const double m = (double)(rowptr[j + 1] - rowptr[j]);
+    total += m * m * m;
+  }
+  auto start = [&](int32_t k) -> int32_t {
+    if (k <= 0) return 0;
+    if (k >= count) return n;
+    const double target = total * (double)k / (double)count;
+    double acc = 0.0;
+    for (int32_t j = 0; j < n; ++j) {
+      if (acc >= target) return j;
+      const double m = (double)(rowptr[j + 1] - rowptr[j]);
+      acc += m * m * m;
+    }
+    return n;
+  };
+  *row_begin = start(rank);
+  *row_end = start(rank + 1);
+  return SUBMAT_OK;
+}
+
 void submat_default_opts(submat_opts* o) {
   if (!o) return;
   o->precision = SUBMAT_PREC_MIXED_F16;
@@ -191,6 +222,8 @@ void submat_default_opts(submat_opts* o) {
   o->root_sign = -1;
   o->grad_deterministic = 0;
   o->grad_wave_mib = 0;
+  o->shard_count = 0;
+  o->shard_rank = 0;
 }
 
 const char* submat_status_string(submat_status s) {
@@ -238,6 +271,12 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   if (o.grad_deterministic != 0 && o.grad_deterministic != 1)
     return fail(SUBMAT_EINVAL, "grad_deterministic must be 0 or 1");
   if (o.grad_wave_mib <= 0) o.grad_wave_mib = SUBMAT_GRAD_WAVE_MIB;
+  if (o.shard_count <= 1) {
+    o.shard_count = 1;
+    if (o.shard_rank != 0) return fail(SUBMAT_EINVAL, "shard_rank must be 0 without shards");
+  } else if (o.shard_rank < 0 || o.shard_rank >= o.shard_count) {
+    return fail(SUBMAT_EINVAL, "shard_rank must lie in [0, shard_count)");
+  }
 
   const int32_t n = csr->n;
   const int64_t nnz = csr->nnz;
@@ -270,6 +309,17 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   P->p = p;
   P->opts = o;
   P->m_max = m_max;
+  {
+    submat_status sst = submat_shard_rows(n, h_rowptr.data(), o.shard_count, o.shard_rank,
+                                          &P->row_begin, &P->row_end);
+    if (sst != SUBMAT_OK) { delete P; return sst; }
+  }
+  P->n_jobs = P->row_end - P->row_begin;
+  sum_m3 = 0.0;
+  for (int32_t j = P->row_begin; j < P->row_end; ++j) {
+    const double len = (double)(h_rowptr[j + 1] - h_rowptr[j]);
+    sum_m3 += len * len * len;
+  }
   P->sum_m3 = sum_m3;
   auto bail = [&](submat_status st) {
     release(P);
@@ -323,18 +373,20 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
     fail(SUBMAT_ENODIAG, "a row does not store its diagonal entry");
     return bail(SUBMAT_ENODIAG);
   }
-  // Rows by decreasing size (longest first), ties by index: counting sort on m.
+  // The plan's rows (its shard) by decreasing size (longest first), ties by index: counting
+  // sort on m.
   std::vector<int32_t> h_m(nb), order(nb);
   if (n > 0) PLAN_TRY(cudaMemcpy(h_m.data(), P->d_m, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
   {
     std::vector<int64_t> start(SUBMAT_MAX_M + 2, 0);
-    for (int32_t j = 0; j < n; ++j) start[SUBMAT_MAX_M - h_m[j]]++;
+    for (int32_t j = P->row_begin; j < P->row_end; ++j) start[SUBMAT_MAX_M - h_m[j]]++;
     int64_t acc = 0;
     for (auto& v : start) { const int64_t c = v; v = acc; acc += c; }
-    for (int32_t j = 0; j < n; ++j) order[start[SUBMAT_MAX_M - h_m[j]]++] = j;
+    for (int32_t j = P->row_begin; j < P->row_end; ++j) order[start[SUBMAT_MAX_M - h_m[j]]++] = j;
   }
-  if (n > 0)
-    PLAN_TRY(cudaMemcpy(P->d_order, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (P->n_jobs > 0)
+    PLAN_TRY(cudaMemcpy(P->d_order, order.data(), P->n_jobs * sizeof(int32_t),
+                        cudaMemcpyHostToDevice));
   P->h_m.assign(h_m.begin(), h_m.begin() + n);
 
   const int mp = std::max(pad_mixed(m_max), pad_fp64(m_max));
@@ -346,7 +398,7 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   stride = (stride + 1023) / 1024 * 1024;
   P->stride = stride;
   const int ctas = (o.precision == SUBMAT_PREC_MIXED_F16) ? mixed_ctas_per_sm() : 1;
-  P->grid = std::max(1, std::min(P->n_sm * ctas, n));
+  P->grid = std::max(1, std::min(P->n_sm * ctas, P->n_jobs));
   PLAN_TRY(cudaMalloc(&P->d_scratch, stride * (size_t)P->grid));
   if (mixed && o.precision == SUBMAT_PREC_MIXED_F16) {
     // TMA descriptors over all CTAs' planes: dims (LD cols, LD rows, planes), 32-byte swizzle
@@ -486,7 +538,7 @@ submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, d
   a.m = P->d_m;
   a.pos = P->d_pos;
   a.order = P->d_order;
-  a.n = P->n;
+  a.n = P->n_jobs;                      // rows of this plan (d_order holds them)
   a.p = P->p;
   a.vals = P->d_saved;
   a.grad_out = grad_out;
@@ -509,9 +561,9 @@ submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, d
       const int64_t cap = (int64_t)P->opts.grad_wave_mib * 1024 * 1024 / (int64_t)sizeof(double);
       P->waves.clear();
       int64_t wave_max = 0;
-      for (int32_t j0 = 0; j0 < P->n;) {
+      for (int32_t j0 = P->row_begin; j0 < P->row_end;) {       // the plan's rows only
         int32_t j1 = j0 + 1;
-        while (j1 < P->n && gofs[j1 + 1] - gofs[j0] <= cap) ++j1;
+        while (j1 < P->row_end && gofs[j1 + 1] - gofs[j0] <= cap) ++j1;
         P->waves.emplace_back(j0, j1);
         wave_max = std::max(wave_max, gofs[j1] - gofs[j0]);
         j0 = j1;
@@ -624,7 +676,7 @@ submat_status submat_get_report(submat_plan_t P, submat_report* r) {
   g_last_error.clear();
   if (!P || !r) return fail(SUBMAT_EINVAL, "NULL argument");
   std::memset(r, 0, sizeof(*r));
-  r->n_rows = P->n;
+  r->n_rows = P->n_jobs;
   r->m_max = P->m_max;
   r->sum_m3 = P->sum_m3;
   if (P->n == 0) return SUBMAT_OK;

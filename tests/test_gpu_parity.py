@@ -343,3 +343,28 @@ def test_positive_root_dense_pattern_is_full_root(sm):
         full = np.real(sl.fractional_matrix_power(dense, 1.0 / p))
         yd = oracle.to_dense(a.n, a.rowptr, a.colind, y)
         assert np.abs(yd - full.T).max() / np.abs(full).max() < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_shards_reproduce_the_whole(sm, precision):
+    """Plans for the shards of a row partition (one GPU each in a multi-GPU run; here the
+    shards run one after another) write disjoint row segments that together equal the
+    unsharded forward bit for bit, and their backward contributions add up to the full
+    gradient."""
+    a = wl.overlap_uniform(n=1200, kappa=1e3)
+    v = torch.tensor(a.vals, device="cuda")
+    w = torch.tensor(wl.random_on_pattern(a, seed=9), device="cuda")
+    full = sm.submat_plan(a.rowptr, a.colind, 2, precision=precision)
+    y = sm.submat_invroot(full, v)
+    g = sm.submat_invroot_backward(full, w)
+    ys = torch.full_like(v, float("nan"))
+    gs = torch.zeros_like(v)
+    for rank in range(3):
+        b, e = sm.shard_rows(a.rowptr, 3, rank)
+        plan = sm.submat_plan(a.rowptr, a.colind, 2, precision=precision, shard=(rank, 3))
+        assert plan.report()["n_rows"] == e - b
+        sm.submat_invroot(plan, v, ys)
+        gs += sm.submat_invroot_backward(plan, w)
+    torch.cuda.synchronize()
+    assert torch.equal(ys, y)
+    assert (gs - g).abs().max().item() <= 1e-12 * g.abs().max().item()
