@@ -8,3 +8,4 @@ from .submatrix import (  # noqa: F401
     divided_differences, submatrix_grad, grad, to_dense, residual_2norm,
 )
 from . import cg  # noqa: F401,E402
+from . import refine  # noqa: F401,E402

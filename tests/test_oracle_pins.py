@@ -392,3 +392,36 @@ def test_pcg_with_exact_inverse_square_root_takes_one_step():
     x, it, rel, true = oracle.cg.solve(rp, ci, v, b, vals_k=k, tol=1e-10)
     assert it == 1 and true <= 1e-10
     np.testing.assert_allclose(x, np.linalg.solve(a, b), rtol=1e-9)
+
+
+# --- global refinement experiment (Sec. 4.5): oracle pins ----------------------------------
+def test_refine_masked_product_brute_force():
+    a = wl.random_sparse_spd(30, 0.25, seed=2)
+    lv = wl.random_on_pattern(a, seed=3)
+    rv = wl.random_on_pattern(a, seed=4)
+    d = oracle.to_dense(a.n, a.rowptr, a.colind, lv) @ oracle.to_dense(a.n, a.rowptr, a.colind, rv)
+    got = oracle.refine.masked_product(a.rowptr, a.colind, lv, rv)
+    for i in range(a.n):
+        for e in range(a.rowptr[i], a.rowptr[i + 1]):
+            assert abs(got[e] - d[i, a.colind[e]]) <= 1e-12 * max(1.0, abs(d[i, a.colind[e]]))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_refine_newton_dense_fixed_point_and_quadratic_convergence(p):
+    """With a dense pattern nothing is truncated: A^(-1/p) is a fixed point, and from a start
+    that commutes with A (a multiple of I inside the convergence region) the error falls
+    quadratically."""
+    rng = np.random.default_rng(p)
+    b_ = rng.standard_normal((16, 16))
+    a = b_ @ b_.T / 16 + 0.5 * np.eye(16)
+    rp, ci, v = _dense_csr(a)
+    lam, vec = np.linalg.eigh(a)
+    z = ((vec * lam ** (-1.0 / p)) @ vec.T).ravel()
+    xs = oracle.refine.refine(rp, ci, v, z, p, 1)
+    np.testing.assert_allclose(xs[1], z, rtol=1e-10, atol=1e-12)
+    start = (np.eye(16) / lam.max() ** (1.0 / p)).ravel()
+    xs = oracle.refine.refine(rp, ci, v, start, p, 12)
+    errs = [oracle.refine.error_on_pattern(rp, ci, v, x, p) for x in xs]
+    assert errs[-1] <= 1e-12
+    k = next(i for i, e in enumerate(errs) if e < 1e-3)
+    assert errs[k + 1] <= 10 * errs[k] ** 2          # quadratic once close
