@@ -75,7 +75,10 @@ typedef struct {
   int32_t k_max;           /* iteration cap of the coupled iteration; default 40         */
   double tol;              /* stop when ||M - I||_F <= tol * sqrt(m) (or when it stops
                               decreasing below 1e-2 sqrt(m)), then do one more X update;
-                              default 1e-4 (mixed) / 1e-7 (FP64); <= 0 selects the default */
+                              the mixed path for p >= 2 also stops once ||M - I||_F <= 0.05
+                              and finishes with a Taylor polynomial of M^(-1/p) on the
+                              carried column instead; default 1e-4 (mixed) / 1e-7 (FP64);
+                              <= 0 selects the default                                    */
   double resid_tol;        /* a row whose FP64 column residual ||e_pos - F^p s_pos||_2
                               exceeds this goes to the FP64 eigendecomposition fallback;
                               default 1e-3                                                */

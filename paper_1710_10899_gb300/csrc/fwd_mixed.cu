@@ -316,6 +316,50 @@ __device__ void vec_task(const VecTask& v) {
   }
 }
 
+// Final step of the p >= 2 path: the Taylor polynomial P(E) = sum_{j<=J} c_j E^j of
+// (I - E)^(-1/p), c_0 = 1, c_j = c_{j-1} (1/p + j - 1) / j, E = I - M, applied ny times to
+// y (FP64 results of double-float products) and p times to u (FP32), by Horner:
+// a <- c_j v + a - M a, j = J-1 .. 0, from a = c_J v.  While both still need applications
+// one pass over M serves both (matvec2_slices).  ay, au: scratch vectors (mp).  All threads.
+constexpr float kTaylorStop = 0.05f;    // iterate until ||M - I||_F <= this (p >= 2)
+constexpr int kTaylorMaxDeg = 12;
+__device__ void taylor_final(const VecTask& v, int J, double* ay, float* au) {
+  const int gt = threadIdx.x, gn = blockDim.x;
+  double cj[kTaylorMaxDeg + 1];
+  cj[0] = 1.0;
+  for (int j = 1; j <= J; ++j) cj[j] = cj[j - 1] * (1.0 / (double)v.p + (double)(j - 1)) / (double)j;
+  for (int app = 0; app < v.p; ++app) {         // u needs p applications, y ny <= p - 1
+    const bool ydo = app < v.ny;
+    for (int i = gt; i < v.mp; i += gn) {
+      if (ydo) ay[i] = i < v.m ? cj[J] * v.y[i] : 0.0;
+      au[i] = i < v.m ? (float)cj[J] * v.u[i] : 0.f;
+    }
+    __syncthreads();
+    for (int j = J - 1; j >= 0; --j) {
+      if (ydo) {
+        for (int i = gt; i < v.mp; i += gn) {
+          float h = 0.f, l = 0.f;
+          if (i < v.m) split_dbl(ay[i], h, l);
+          v.yh[i] = h;
+          v.yl[i] = l;
+        }
+        __syncthreads();
+        matvec2_slices<2, 0, true>(v.q, v.plane, v.ld, v.e, v.yh, v.yl, v.my, au, v.t, v.m, v.mp);
+        for (int i = gt; i < v.m; i += gn) ay[i] = cj[j] * v.y[i] + (ay[i] - v.my[i]);
+      } else {
+        matvec_slices_f32<3, 8, 0>(v.q, v.plane, v.ld, ldexpf(1.f, v.e - 7), au, v.t, v.m, v.mp);
+      }
+      for (int i = gt; i < v.m; i += gn) au[i] = (float)cj[j] * v.u[i] + (au[i] - v.t[i]);
+      __syncthreads();
+    }
+    for (int i = gt; i < v.m; i += gn) {
+      if (ydo) v.y[i] = ay[i];
+      v.u[i] = au[i];
+    }
+    __syncthreads();
+  }
+}
+
 // Largest eigenvalue of the SPD X (power method, FP32, two leading planes).
 __device__ float power_max_slices(const __half* q, size_t plane, int ld, float scale, int m,
                                   int mp, float* a_s, float* b_s, float* red_s, int iters) {
@@ -1034,11 +1078,13 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
                  {hb + 4 * NSL * plane, e_m, plane_base + 20}};
     // vectors carried for p >= 2 and their scratch, in the last plane (32 LD bytes)
     double* yg = reinterpret_cast<double*>(hb + 34 * plane);     // column pos of X_k (FP64)
-    float* ug = reinterpret_cast<float*>(yg + LD);               // X_k^p M_0 e_pos
+    float* ug = reinterpret_cast<float*>(yg + LD);               // residual vector
     float* yhg = ug + LD;
     float* ylg = yhg + LD;
     double* myg = reinterpret_cast<double*>(ylg + LD);
     float* tg = reinterpret_cast<float*>(myg + LD);
+    double* ayg = reinterpret_cast<double*>(tg + LD);            // Horner accumulators of
+    float* aug = reinterpret_cast<float*>(ayg + LD);             // the final step
 
     const double lam = gather_submatrix(a.rowptr, a.colind, a.vals_in, j, m, R_s, S, red_s);
     const double inv_lam = 1.0 / lam;
@@ -1141,6 +1187,8 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     // eigenvalue from 1); X_{k+1} = X_k T_k (tracked as vectors for p >= 2, a product for
     // p = 1), M_{k+1} = T_k^p M_k as p products with M_k as the A operand.
     while (!bad) {
+      // p >= 2: close enough to I for the final Taylor step (see below)
+      if (track && nrm2 <= kTaylorStop * kTaylorStop) break;
       const ScaledStep st = scaled_step(fmaxf(lo, 1.f - sqrtf(nrm2)), p);
       io.c = st.c;
       io.alpha = st.alpha;
@@ -1207,7 +1255,12 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     }
     if (stop) break;
 
-    // last step: Newton's T = ((p+1) I - M)/p, whose first-order part is M^(-1/p)
+    // last step.  p >= 2: X_K M_K^(-1/p) is the limit (M_K = X_K^p M_0, all commuting), so
+    // the carried column takes M_K^(-1/p) = (I - E)^(-1/p), E = I - M_K, as its Taylor
+    // polynomial of degree J in E (Horner, one pass over M_K per degree), J chosen from
+    // ||E||_2 <= ||E||_F so that the tail is below 1e-10; this lets the iteration stop at
+    // ||E||_F <= kTaylorStop instead of converging to the rounding floor (one GEMM iteration
+    // fewer on average).  p = 1: Newton's X (2I - M) as a product, then FP64 refinement.
     double resid = 1e300;
     float kest = 0.f;
     const double c = pow(lam, -1.0 / (double)p);               // F = c X
@@ -1221,7 +1274,12 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
         ug[i] = h + l;
       }
       __syncthreads();
-      vec_task<0>(vec_of(B3[mi], 1.0 / (double)p, (double)(p + 1), true));
+      const float eps = sqrtf(nrm2);
+      int J = 1;
+      while (J < kTaylorMaxDeg &&
+             !(powf(eps, (float)(J + 1)) <= 1e-10f * (1.f - eps)))
+        ++J;
+      taylor_final(vec_of(B3[mi], 0.0, 0.0, true), J, ayg, aug);
       // column pos of the result (lambda_bar^(-1/p) X e_pos, or lambda_bar^(1/p) X^(p-1)
       // M_0 e_pos for A^(1/p)) and the residual F^p s_pos - e_pos = u - e_pos of
       // F = lambda_bar^(-1/p) X
