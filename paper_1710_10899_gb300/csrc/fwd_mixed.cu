@@ -320,16 +320,20 @@ __device__ void vec_task(const VecTask& v) {
 // (I - E)^(-1/p), c_0 = 1, c_j = c_{j-1} (1/p + j - 1) / j, E = I - M, applied ny times to
 // y (FP64 results of double-float products) and p times to u (FP32), by Horner:
 // a <- c_j v + a - M a, j = J-1 .. 0, from a = c_J v.  While both still need applications
-// one pass over M serves both (matvec2_slices).  ay, au: scratch vectors (mp).  All threads.
+// one pass over M serves both (matvec2_slices); the applications to u alone use degree Ju
+// (the residual check needs far less accuracy than the column).  ay, au: scratch vectors
+// (mp).  All threads.
 constexpr float kTaylorStop = 0.05f;    // iterate until ||M - I||_F <= this (p >= 2)
 constexpr int kTaylorMaxDeg = 12;
-__device__ void taylor_final(const VecTask& v, int J, double* ay, float* au) {
+__device__ void taylor_final(const VecTask& v, int Jy, int Ju, double* ay, float* au) {
   const int gt = threadIdx.x, gn = blockDim.x;
   double cj[kTaylorMaxDeg + 1];
   cj[0] = 1.0;
-  for (int j = 1; j <= J; ++j) cj[j] = cj[j - 1] * (1.0 / (double)v.p + (double)(j - 1)) / (double)j;
+  for (int j = 1; j <= kTaylorMaxDeg; ++j)
+    cj[j] = cj[j - 1] * (1.0 / (double)v.p + (double)(j - 1)) / (double)j;
   for (int app = 0; app < v.p; ++app) {         // u needs p applications, y ny <= p - 1
     const bool ydo = app < v.ny;
+    const int J = ydo ? Jy : Ju;
     for (int i = gt; i < v.mp; i += gn) {
       if (ydo) ay[i] = i < v.m ? cj[J] * v.y[i] : 0.0;
       au[i] = i < v.m ? (float)cj[J] * v.u[i] : 0.f;
@@ -1275,11 +1279,12 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
       }
       __syncthreads();
       const float eps = sqrtf(nrm2);
-      int J = 1;
-      while (J < kTaylorMaxDeg &&
-             !(powf(eps, (float)(J + 1)) <= 1e-10f * (1.f - eps)))
-        ++J;
-      taylor_final(vec_of(B3[mi], 0.0, 0.0, true), J, ayg, aug);
+      auto degree = [&](float target) {      // tail eps^(J+1) / (1 - eps) <= target
+        int J = 1;
+        while (J < kTaylorMaxDeg && !(powf(eps, (float)(J + 1)) <= target * (1.f - eps))) ++J;
+        return J;
+      };
+      taylor_final(vec_of(B3[mi], 0.0, 0.0, true), degree(1e-10f), degree(1e-6f), ayg, aug);
       // column pos of the result (lambda_bar^(-1/p) X e_pos, or lambda_bar^(1/p) X^(p-1)
       // M_0 e_pos for A^(1/p)) and the residual F^p s_pos - e_pos = u - e_pos of
       // F = lambda_bar^(-1/p) X
