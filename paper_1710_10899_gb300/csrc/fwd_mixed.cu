@@ -5,10 +5,12 @@
 //   M_0 = S/lambda_bar, X_0 = I; coupled iteration for the inverse p-th root
 //       X_{k+1} = X_k T_k,  M_{k+1} = T_k^p M_k
 //   (the coupled form of the Newton iteration of Bini, Higham and Meini cited in Sec. 2)
-//   with spectrally scaled steps T_k = c_k (alpha_k I - M_k) (scaled_step.cuh), until
-//   ||M - I||_F <= tol sqrt(m), then one Newton update X T, T = ((p+1) I - M)/p;
-//   F = lambda_bar^(-1/p) X;
-//   FP64 column residual (refine.cuh) and condition estimate; write column pos_j.
+//   with spectrally scaled steps T_k = c_k (alpha_k I - M_k) (scaled_step.cuh); for p >= 2
+//   only column pos_j of X is carried (a vector), until ||M - I||_F <= 0.05 (or the tol
+//   rule), then X M^(-1/p) with M^(-1/p) as a Taylor polynomial in I - M on that column
+//   (taylor_final); for p = 1 X is a product, until ||M - I||_F <= tol sqrt(m), then one
+//   Newton update X (2I - M) and FP64 refinement of the column (refine.cuh);
+//   F = lambda_bar^(-1/p) X; column residual and condition estimate; write column pos_j.
 //
 // Arithmetic.  Rounding errors made in any iteration persist in the coupled iteration's
 // limit, so every GEMM must be accurate to well below the 1e-6 target, and the tensor
@@ -31,20 +33,22 @@
 //
 // GEMM engines (template parameter TC):
 //   TC = true  (default): tcgen05.mma kind::f16, M = 128, N = 96, the five level
-//              accumulators in one 480-column TMEM buffer, drained in two phases (levels
-//              combined into shared memory, TMEM released, then the affine step and the
-//              stores) so the next tile's MMAs overlap the second phase; operands moved by
-//              TMA (SWIZZLE_32B, 16-wide k-slices) through a 3-stage mbarrier pipeline.
-//              Roles: warps 0-7 run the epilogue (two per TMEM lane quarter), warp 8
-//              issues TMA, warp 9 issues MMAs (320 threads).
+//              accumulators in one 480-column TMEM buffer, drained in phases (levels
+//              combined into shared memory and TMEM released; the affine step and the
+//              stores; the mirror images) so the next tile's MMAs overlap the later
+//              phases; operands moved by TMA (SWIZZLE_32B, 16-wide k-slices) through a
+//              3-stage mbarrier pipeline.  Roles: warps 0-7 run the epilogue (two per TMEM
+//              lane quarter), warp 8 issues TMA, warp 9 issues MMAs, warps 10-11 apply the
+//              iteration's step to the carried column (384 threads).
 //              All working matrices are symmetric, so a row-major B read as K-major
 //              gives B^T = B to rounding: the engine computes A B^T.
 //   TC = false: mma.sync m16n8k16 on 64 x 64 tiles with a cp.async pipeline (the legacy
 //              tensor path, kept as the baseline the tcgen05 engine is measured against).
 //
-// Working matrices live in a per-CTA global scratch: 34 planes of LD x LD halves per CTA
-// (LD = the plan's largest order padded to 64): X, T, M (two buffers each) x 5 planes, then
-// the gathered S_j in FP64 in the last four planes' space.  A submatrix of order m uses the
+// Working matrices live in a per-CTA global scratch: 35 planes of LD x LD halves per CTA
+// (LD = the plan's largest order padded to 64): two X buffers (p = 1) and three buffers for
+// M_k and the partial products, 5 planes each, the gathered S_j in FP64 in four planes'
+// space, and one plane for the carried vectors.  A submatrix of order m uses the
 // leading mp x mp block (mp = m padded to 16 for tcgen05, 64 for mma.sync); its padding
 // rows/columns stay exactly zero.  Rows of a tile beyond mp may hold older data: they only
 // reach output entries beyond mp, which are never stored.
