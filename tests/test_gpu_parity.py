@@ -368,3 +368,19 @@ def test_shards_reproduce_the_whole(sm, precision):
     torch.cuda.synchronize()
     assert torch.equal(ys, y)
     assert (gs - g).abs().max().item() <= 1e-12 * g.abs().max().item()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_taylor_finish_without_products(sm, p, sign):
+    """Submatrices already within the stopping distance of I (||M_0 - I||_F <= 0.05) take
+    no GEMM iteration: the Taylor finish on the carried column alone gives the root."""
+    rng = np.random.default_rng(20 + p)
+    n = 300
+    off = rng.uniform(-1e-3, 1e-3, n - 1)
+    a = wl.dense_to_csr(np.eye(n) + np.diag(off, 1) + np.diag(off, -1))
+    plan = sm.submat_plan(a.rowptr, a.colind, p, precision="mixed", root_sign=sign)
+    y = sm.submat_invroot(plan, torch.tensor(a.vals, device="cuda"), sync=True).cpu().numpy()
+    assert plan.report()["iters_max"] == 0
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, p, sign=sign)
+    assert row_errors(a, y, ref, range(a.n)).max() <= TOL["mixed"]
