@@ -15,6 +15,7 @@
 #include <algorithm>
 #include "common.cuh"
 #include "jacobi.cuh"
+#include "jacobi_df.cuh"
 
 namespace submat {
 namespace {
@@ -70,7 +71,17 @@ __global__ void __launch_bounds__(kThreads) fallback_kernel(FwdArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
+// Packed upper triangle of a submatrix held in shared memory by the backward's Jacobi:
+// orders up to 198 (the rest of the kernel's shared memory and the gather's static row
+// extents leave this much of the 227 KB).
+constexpr int kPackedMax = 198 * 199 / 2;
+
+// The backward's per-step Jacobi work is latency-bound at 8 warps; 16 warps (128 registers
+// each, the whole register file) hide twice as much.
+constexpr int kBwdThreads = 512;
+static_assert(kBwdThreads / 32 <= kMaxWarps, "reduction scratch");
+
+__global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* cs_s = reinterpret_cast<double*>(smem_raw);               // SUBMAT_MAX_M
   double* al_s = cs_s + SUBMAT_MAX_M;                                 // alpha = lambda^(1/p)
@@ -79,6 +90,7 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
   double* red_s = w_s + SUBMAT_MAX_M;                                 // kRedDoubles
   int32_t* pair_s = reinterpret_cast<int32_t*>(red_s + kRedDoubles);  // SUBMAT_MAX_M
   int32_t* R_s = pair_s + SUBMAT_MAX_M;                               // SUBMAT_MAX_M
+  float2* P_s = reinterpret_cast<float2*>(R_s + SUBMAT_MAX_M);        // kPackedMax
   __shared__ int job_s;
   __shared__ int bad_s;
   char* scr = a.scratch + (size_t)blockIdx.x * a.scratch_stride;
@@ -96,7 +108,33 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(BwdArgs a) {
     double* V = A + (size_t)m * m;
     double* W = V + (size_t)m * m;
     gather_dense(a.rowptr, a.colind, a.vals, j, m, R_s, A, red_s);
-    const int sweeps = jacobi_eig(A, V, m, pair_s, cs_s, red_s);
+    // the eigendecomposition in double-float (jacobi_df.cuh): with A's upper triangle packed
+    // in shared memory when it fits (eigenvectors transposed in W), else in place in A, V
+    int sweeps;
+    if (m * (m + 1) / 2 <= kPackedMax) {
+      for (int e = tid; e < m * m; e += blockDim.x) {
+        const int r = e / m, c = e - r * m;
+        if (r <= c) P_s[jdf::pidx(r, c, m)] = jdf::split(A[e]);
+      }
+      __syncthreads();
+      float2* Vt = reinterpret_cast<float2*>(W);
+      sweeps = jdf::jacobi_eig_df_packed(P_s, Vt, m, pair_s, reinterpret_cast<float*>(cs_s), red_s);
+      for (int e = tid; e < m * m; e += blockDim.x) {
+        const int i = e / m, k = e - i * m;
+        V[e] = jdf::join(Vt[k * m + i]);
+        if (i == k) A[e] = jdf::join(P_s[jdf::pidx(i, i, m)]);
+      }
+    } else {
+      float2* A2 = reinterpret_cast<float2*>(A);
+      float2* V2 = reinterpret_cast<float2*>(V);
+      for (int e = tid; e < m * m; e += blockDim.x) A2[e] = jdf::split(A[e]);
+      __syncthreads();
+      sweeps = jdf::jacobi_eig_df(A2, V2, m, pair_s, reinterpret_cast<float*>(cs_s), red_s);
+      for (int e = tid; e < m * m; e += blockDim.x) {
+        A[e] = jdf::join(A2[e]);
+        V[e] = jdf::join(V2[e]);
+      }
+    }
     if (tid == 0) bad_s = sweeps < 0 ? 1 : 0;
     __syncthreads();
     const double* g = a.grad_out + a.rowptr[j];
@@ -258,7 +296,8 @@ size_t smem_fallback() {
   return (2 * SUBMAT_MAX_M + kRedDoubles) * sizeof(double) + 2 * SUBMAT_MAX_M * sizeof(int32_t);
 }
 size_t smem_backward() {
-  return (4 * SUBMAT_MAX_M + kRedDoubles) * sizeof(double) + 2 * SUBMAT_MAX_M * sizeof(int32_t);
+  return (4 * SUBMAT_MAX_M + kRedDoubles) * sizeof(double) + 2 * SUBMAT_MAX_M * sizeof(int32_t) +
+         kPackedMax * sizeof(float2);
 }
 size_t scratch_eig(int mp) { return 3 * (size_t)mp * mp * sizeof(double); }
 
@@ -267,7 +306,7 @@ cudaError_t launch_fallback(const FwdArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_backward(const BwdArgs& a, int grid, cudaStream_t s) {
-  backward_kernel<<<grid, kThreads, smem_backward(), s>>>(a);
+  backward_kernel<<<grid, kBwdThreads, smem_backward(), s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t set_attr_eig() {

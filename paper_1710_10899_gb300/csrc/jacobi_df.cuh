@@ -1,0 +1,294 @@
+// Cyclic Jacobi eigendecomposition of one symmetric submatrix per CTA with the matrix and
+// the eigenvectors held as double-floats (FP32 pairs, ~44 significant bits) (internal
+// header).  The O(m^3) rotation updates run on the FP32 units: an FP64 operation costs
+// 64 FP32 operations' time on this GPU, and a double-float rotation update takes about 20
+// FP32 operations for the 2 of FP64.  The O(m) rotation angles per step are computed in
+// FP64.  Same ordering and rotation as jacobi.cuh (round-robin pairs; the symmetric 2x2 Schur
+// decomposition of Golub & Van Loan, Alg. 8.4.1); it stops at off(A) <= 1e-12 ||A||_F or,
+// below 1e-9 ||A||_F, once a sweep shrinks off(A) by less than half (the rounding floor of
+// double-floats; FP64's 1e-14 bound they cannot reach).
+#pragma once
+#include "common.cuh"
+#include "slices.cuh"
+
+namespace submat {
+namespace jdf {
+
+constexpr int kMaxSweeps = 30;
+constexpr int kVtU = 8;        // eigenvector elements in flight per thread (packed variant)
+
+__device__ __forceinline__ float2 split(double d) {
+  const float h = (float)d;
+  return make_float2(h, (float)(d - (double)h));
+}
+__device__ __forceinline__ double join(float2 a) { return (double)a.x + (double)a.y; }
+
+// c a - s b for double-floats (products exact in their leading parts, cross terms added).
+__device__ __forceinline__ float2 rot(float2 c, float2 a, float2 s, float2 b) {
+  const float p1 = c.x * a.x;
+  float e1 = fmaf(c.x, a.x, -p1);
+  e1 = fmaf(c.x, a.y, fmaf(c.y, a.x, e1));
+  const float p2 = s.x * b.x;
+  float e2 = fmaf(s.x, b.x, -p2);
+  e2 = fmaf(s.x, b.y, fmaf(s.y, b.x, e2));
+  float h, l;
+  slc::two_sum(p1, -p2, h, l);
+  l = l + (e1 - e2);
+  const float r = h + l;
+  return make_float2(r, l - (r - h));
+}
+
+// Eigendecomposition of the symmetric m x m matrix A (double-floats, ld m, global) in place:
+// on return A's diagonal holds the eigenvalues and V (ld m) the eigenvectors (columns).
+// pair_s: 2*ceil(m/2) ints, cs_s: 4*ceil(m/2) floats (shared), red_s: kRedDoubles doubles.
+// Returns the sweeps used, or -1 if A holds a non-finite value.
+static __device__ int jacobi_eig_df(float2* __restrict__ A, float2* __restrict__ V, int m,
+                                    int* pair_s, float* cs_s, double* red_s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < m * m; e += blockDim.x)
+    V[e] = make_float2((e / m == e % m) ? 1.f : 0.f, 0.f);
+  __syncthreads();
+  const int mm = m + (m & 1);
+  const int np = mm / 2;
+  int sweep = 0;
+  double prev = 1.7e308;
+  for (; sweep < kMaxSweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const double v = (double)A[e].x;
+      tot += v * v;
+      if (e / m != e % m) off += v * v;
+    }
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if (lane == 0) { red_s[warp] = off; red_s[kMaxWarps + warp] = tot; }
+    __syncthreads();
+    double so = 0.0, st = 0.0;
+    for (int w = 0; w < nwarps(); ++w) { so += red_s[w]; st += red_s[kMaxWarps + w]; }
+    __syncthreads();
+    if (!(st <= 1.7e308)) return -1;     // NaN or infinity somewhere in A
+    if (m == 1 || !(so > 1e-24 * st)) break;       // off(A) <= 1e-12 ||A||_F
+    // at double-float rounding level (about 2^-44 ||A|| per entry, so for larger m the
+    // bound above is out of reach) a sweep no longer shrinks off(A) quadratically
+    if (so <= 1e-18 * st && so > 0.25 * prev) break;
+    prev = so;
+    for (int s = 0; s < mm - 1; ++s) {
+      for (int k = tid; k < np; k += blockDim.x) {
+        int p, q;
+        if (k == 0) { p = s; q = mm - 1; }
+        else { p = (s + k) % (mm - 1); q = (s - k + mm - 1) % (mm - 1); }
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, sn = 0.0;
+        if (q < m) {
+          const double apq = join(A[p * m + q]);
+          if (apq != 0.0) {
+            const double tau = (join(A[q * m + q]) - join(A[p * m + p])) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        }
+        pair_s[2 * k] = p;
+        pair_s[2 * k + 1] = q;
+        const float2 cd = split(c), sd = split(sn);
+        cs_s[4 * k] = cd.x;
+        cs_s[4 * k + 1] = cd.y;
+        cs_s[4 * k + 2] = sd.x;
+        cs_s[4 * k + 3] = sd.y;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int e = tid; e < np * m; e += blockDim.x) {
+        const int k = e / m, i = e % m;
+        const int p = pair_s[2 * k], q = pair_s[2 * k + 1];
+        if (q >= m) continue;
+        const float2 c = make_float2(cs_s[4 * k], cs_s[4 * k + 1]);
+        const float2 sn = make_float2(cs_s[4 * k + 2], cs_s[4 * k + 3]);
+        if (sn.x == 0.f) continue;
+        const float2 nc = make_float2(-c.x, -c.y);
+        const float2 ap = A[i * m + p], aq = A[i * m + q];
+        A[i * m + p] = rot(c, ap, sn, aq);
+        A[i * m + q] = rot(sn, ap, nc, aq);              // s ap + c aq
+        const float2 vp = V[i * m + p], vq = V[i * m + q];
+        V[i * m + p] = rot(c, vp, sn, vq);
+        V[i * m + q] = rot(sn, vp, nc, vq);
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = tid; e < np * m; e += blockDim.x) {
+        const int k = e / m, i = e % m;
+        const int p = pair_s[2 * k], q = pair_s[2 * k + 1];
+        if (q >= m) continue;
+        const float2 c = make_float2(cs_s[4 * k], cs_s[4 * k + 1]);
+        const float2 sn = make_float2(cs_s[4 * k + 2], cs_s[4 * k + 3]);
+        if (sn.x == 0.f) continue;
+        const float2 nc = make_float2(-c.x, -c.y);
+        const float2 ap = A[p * m + i], aq = A[q * m + i];
+        A[p * m + i] = rot(c, ap, sn, aq);
+        A[q * m + i] = rot(sn, ap, nc, aq);
+      }
+      __syncthreads();
+    }
+  }
+  return sweep;
+}
+
+// Index of (r, c), r <= c, in the row-packed upper triangle of an m x m symmetric matrix.
+__device__ __forceinline__ int pidx(int r, int c, int m) { return r * m - (r * (r - 1)) / 2 + (c - r); }
+__device__ __forceinline__ int pidx_sym(int a, int b, int m) {
+  return a <= b ? pidx(a, b, m) : pidx(b, a, m);
+}
+
+// The same decomposition with A's upper triangle packed in shared memory (P, m(m+1)/2
+// double-floats) and the eigenvectors transposed in global memory (Vt, ld m: row k = the
+// k-th eigenvector), so every step touches only shared memory and coalesced rows.  A step's
+// disjoint rotations act on 2 x 2 blocks of A: block (k, l), rows of pair k and columns of
+// pair l, becomes J_k^T B J_l, J = [[c, s], [-s, c]] (one thread per block of the upper block
+// triangle, so every packed entry has one writer).  On return P's diagonal holds the
+// eigenvalues.  Same returns as jacobi_eig_df.
+static __device__ int jacobi_eig_df_packed(float2* __restrict__ P, float2* __restrict__ Vt,
+                                           int m, int* pair_s, float* cs_s, double* red_s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < m * m; e += blockDim.x)
+    Vt[e] = make_float2((e / m == e % m) ? 1.f : 0.f, 0.f);
+  __syncthreads();
+  const int mm = m + (m & 1);
+  const int np = mm / 2;
+  int sweep = 0;
+  double prev = 1.7e308;
+  for (; sweep < kMaxSweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int r = e / m, c = e - r * m;
+      if (r > c) continue;
+      const double v = (double)P[pidx(r, c, m)].x;
+      tot += (r == c ? 1.0 : 2.0) * v * v;
+      if (r != c) off += 2.0 * v * v;
+    }
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if (lane == 0) { red_s[warp] = off; red_s[kMaxWarps + warp] = tot; }
+    __syncthreads();
+    double so = 0.0, st = 0.0;
+    for (int w = 0; w < nwarps(); ++w) { so += red_s[w]; st += red_s[kMaxWarps + w]; }
+    __syncthreads();
+    if (!(st <= 1.7e308)) return -1;     // NaN or infinity somewhere in A
+    if (m == 1 || !(so > 1e-24 * st)) break;       // off(A) <= 1e-12 ||A||_F
+    // at double-float rounding level (about 2^-44 ||A|| per entry, so for larger m the
+    // bound above is out of reach) a sweep no longer shrinks off(A) quadratically
+    if (so <= 1e-18 * st && so > 0.25 * prev) break;
+    prev = so;
+    for (int s = 0; s < mm - 1; ++s) {
+      for (int k = tid; k < np; k += blockDim.x) {
+        int p, q;
+        if (k == 0) { p = s; q = mm - 1; }
+        else { p = (s + k) % (mm - 1); q = (s - k + mm - 1) % (mm - 1); }
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, sn = 0.0;
+        if (q < m) {
+          const double apq = join(P[pidx(p, q, m)]);
+          if (apq != 0.0) {
+            const double tau = (join(P[pidx(q, q, m)]) - join(P[pidx(p, p, m)])) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        }
+        pair_s[2 * k] = p;
+        pair_s[2 * k + 1] = q;
+        const float2 cd = split(c), sd = split(sn);
+        cs_s[4 * k] = cd.x;
+        cs_s[4 * k + 1] = cd.y;
+        cs_s[4 * k + 2] = sd.x;
+        cs_s[4 * k + 3] = sd.y;
+      }
+      __syncthreads();
+      // blocks (k, l), k <= l, of the upper block triangle
+      for (int e = tid; e < np * np; e += blockDim.x) {
+        const int k = e / np, l = e - k * np;
+        if (k > l) continue;
+        const int pk = pair_s[2 * k], qk = pair_s[2 * k + 1];
+        const int pl = pair_s[2 * l], ql = pair_s[2 * l + 1];
+        const bool hk = qk < m, hl = ql < m;            // pair has its second index
+        const float2 ck = make_float2(cs_s[4 * k], cs_s[4 * k + 1]);
+        const float2 sk = make_float2(cs_s[4 * k + 2], cs_s[4 * k + 3]);
+        const float2 cl = make_float2(cs_s[4 * l], cs_s[4 * l + 1]);
+        const float2 sl = make_float2(cs_s[4 * l + 2], cs_s[4 * l + 3]);
+        const float2 z = make_float2(0.f, 0.f);
+        const float2 nck = make_float2(-ck.x, -ck.y), ncl = make_float2(-cl.x, -cl.y);
+        if (k == l) {
+          if (!hk || sk.x == 0.f) continue;               // no rotation
+          const float2 b00 = P[pidx(pk, pk, m)], b01 = P[pidx(pk, qk, m)], b11 = P[pidx(qk, qk, m)];
+          // C = B J, then B' = J^T C (symmetric)
+          const float2 c00 = rot(ck, b00, sk, b01), c01 = rot(sk, b00, nck, b01);
+          const float2 c10 = rot(ck, b01, sk, b11), c11 = rot(sk, b01, nck, b11);
+          P[pidx(pk, pk, m)] = rot(ck, c00, sk, c10);
+          P[pidx(pk, qk, m)] = rot(ck, c01, sk, c11);
+          P[pidx(qk, qk, m)] = rot(sk, c01, nck, c11);
+          continue;
+        }
+        const bool rk = hk && sk.x != 0.f, rl = hl && sl.x != 0.f;   // rotations applied
+        if (!rk && !rl) continue;
+        const int i00 = pidx_sym(pk, pl, m);
+        const int i01 = hl ? pidx_sym(pk, ql, m) : 0;
+        const int i10 = hk ? pidx_sym(qk, pl, m) : 0;
+        const int i11 = (hk && hl) ? pidx_sym(qk, ql, m) : 0;
+        float2 b00 = P[i00];
+        float2 b01 = hl ? P[i01] : z;
+        float2 b10 = hk ? P[i10] : z;
+        float2 b11 = (hk && hl) ? P[i11] : z;
+        if (rl) {                                          // columns: B J_l
+          const float2 t00 = rot(cl, b00, sl, b01), t01 = rot(sl, b00, ncl, b01);
+          const float2 t10 = rot(cl, b10, sl, b11), t11 = rot(sl, b10, ncl, b11);
+          b00 = t00; b01 = t01; b10 = t10; b11 = t11;
+        }
+        if (rk) {                                          // rows: J_k^T B
+          const float2 t00 = rot(ck, b00, sk, b10), t10 = rot(sk, b00, nck, b10);
+          const float2 t01 = rot(ck, b01, sk, b11), t11 = rot(sk, b01, nck, b11);
+          b00 = t00; b01 = t01; b10 = t10; b11 = t11;
+        }
+        P[i00] = b00;
+        if (hl) P[i01] = b01;
+        if (hk) P[i10] = b10;
+        if (hk && hl) P[i11] = b11;
+      }
+      // eigenvectors: rows p, q of Vt, kVtU elements per thread loaded before any is
+      // stored (the rows live in global memory: one round trip per kVtU elements)
+      for (int e0 = tid; e0 < np * m; e0 += kVtU * blockDim.x) {
+        float2 vp[kVtU], vq[kVtU];
+        int ip[kVtU], iq[kVtU], kk[kVtU];
+#pragma unroll
+        for (int u = 0; u < kVtU; ++u) {
+          const int e = e0 + u * blockDim.x;
+          kk[u] = -1;
+          if (e < np * m) {
+            const int k = e / m, i = e - k * m;
+            const int p = pair_s[2 * k], q = pair_s[2 * k + 1];
+            if (q < m && cs_s[4 * k + 2] != 0.f) {
+              kk[u] = k;
+              ip[u] = p * m + i;
+              iq[u] = q * m + i;
+              vp[u] = Vt[ip[u]];
+              vq[u] = Vt[iq[u]];
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kVtU; ++u) {
+          if (kk[u] < 0) continue;
+          const int k = kk[u];
+          const float2 c = make_float2(cs_s[4 * k], cs_s[4 * k + 1]);
+          const float2 sn = make_float2(cs_s[4 * k + 2], cs_s[4 * k + 3]);
+          const float2 nc = make_float2(-c.x, -c.y);
+          Vt[ip[u]] = rot(c, vp[u], sn, vq[u]);
+          Vt[iq[u]] = rot(sn, vp[u], nc, vq[u]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  return sweep;
+}
+
+}  // namespace jdf
+}  // namespace submat
