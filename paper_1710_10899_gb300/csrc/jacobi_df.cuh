@@ -203,10 +203,16 @@ static __device__ int jacobi_eig_df_packed(float2* __restrict__ P, float2* __res
         cs_s[4 * k + 3] = sd.y;
       }
       __syncthreads();
-      // blocks (k, l), k <= l, of the upper block triangle
-      for (int e = tid; e < np * np; e += blockDim.x) {
-        const int k = e / np, l = e - k * np;
-        if (k > l) continue;
+      // blocks (k, l), k <= l, of the upper block triangle, enumerated row by row:
+      // block t lies in row k with T(k) <= t < T(k+1), T(k) = k (2 np - k + 1) / 2
+      const int nblk = np * (np + 1) / 2;
+      const float b2 = (float)(2 * np + 1);
+      for (int e = tid; e < nblk; e += blockDim.x) {
+        int k = (int)((b2 - sqrtf(b2 * b2 - 8.f * (float)e)) * 0.5f);
+        k = max(0, min(k, np - 1));
+        while (k > 0 && k * (2 * np - k + 1) / 2 > e) --k;
+        while (k + 1 < np && (k + 1) * (2 * np - k) / 2 <= e) ++k;
+        const int l = k + (e - k * (2 * np - k + 1) / 2);
         const int pk = pair_s[2 * k], qk = pair_s[2 * k + 1];
         const int pl = pair_s[2 * l], ql = pair_s[2 * l + 1];
         const bool hk = qk < m, hl = ql < m;            // pair has its second index
