@@ -193,9 +193,11 @@ SUBMAT_API submat_status submat_invroot_host(submat_plan_t plan, const double* v
  * f(x) = x^(root_sign/p)):
  * grad_in = dL/dvals for L = sum(grad_out * vals_out) of the last forward, with respect to
  * A's stored values, the (r,c)/(c,r) pair sharing one symmetric perturbation.  For each row
- * j the submatrix is regathered from the saved vals_in and decomposed again in FP64
- * (recomputation, no stored iterates).  grad_out and grad_in are device arrays of nnz
- * doubles; grad_in is overwritten.  Returns SUBMAT_ENOFWD if no forward ran on this plan.
+ * j the submatrix is regathered from the saved vals_in and decomposed again (recomputation,
+ * no stored iterates) by a cyclic Jacobi with the matrix and eigenvectors held as
+ * double-floats (FP32 pairs, ~44 significant bits; the rotation angles, the divided
+ * differences and the products with the eigenvectors in FP64).  grad_out and grad_in are
+ * device arrays of nnz doubles; grad_in is overwritten.  Returns SUBMAT_ENOFWD if no forward ran on this plan.
  * With opts.grad_deterministic = 1 the per-submatrix gradients G_j of a wave of rows are
  * stored, and each entry (r, c) then adds G_j(r, c) over the wave's rows j whose patterns
  * hold both r and c (the transposed map of the plan: j in R_r and R_c), without atomics.
