@@ -35,7 +35,8 @@ extern "C" {
 typedef enum {
   SUBMAT_OK = 0,
   SUBMAT_EINVAL = 1,    /* bad argument: NULL pointer, p < 1, unsorted/duplicate/out-of-range
-                           column index, negative sizes, vals_out aliasing vals_in        */
+                           column index, negative sizes, vals_out aliasing vals_in or
+                           grad_in aliasing grad_out                                      */
   SUBMAT_ENODIAG = 2,   /* a row does not store its diagonal entry (Alg. 2 needs
                            R.indexof(j))                                                  */
   SUBMAT_ENOTSYM = 3,   /* the pattern is not symmetric                                    */
@@ -154,7 +155,8 @@ SUBMAT_API void submat_default_opts(submat_opts* opts);
 
 /*
  * Build a plan for A's pattern and the root order p >= 1 (Alg. 1, index part).
- * Checks the pattern (SUBMAT_EINVAL / ENODIAG / ENOTSYM / ETOOBIG), computes m_j and
+ * Checks the pattern (SUBMAT_EINVAL / ENODIAG / ENOTSYM / ETOOBIG; n > nnz means some row
+ * lacks its diagonal: ENODIAG), computes m_j and
  * pos_j on the device, orders the rows by decreasing m_j for the persistent scheduler,
  * and allocates the per-CTA working storage.  The plan keeps device copies of rowptr and
  * colind; the caller's arrays may be freed afterwards.  opts may be NULL (defaults).
@@ -180,7 +182,8 @@ SUBMAT_API submat_status submat_invroot(submat_plan_t plan, const double* vals_i
  * the copies asynchronous) to plan-owned device memory on the stream, runs
  * submat_invroot, copies the result back into vals_out (host, nnz doubles) and
  * synchronises the stream.  The device buffers are allocated on the first call and kept
- * by the plan.  Returns SUBMAT_ENOTSPD like submat_invroot with sync != 0.
+ * by the plan.  Returns SUBMAT_ENOTSPD and SUBMAT_ETIMEOUT like submat_invroot with
+ * sync != 0.
  */
 SUBMAT_API submat_status submat_invroot_host(submat_plan_t plan, const double* vals_in,
                                              double* vals_out, void* stream);
@@ -197,7 +200,7 @@ SUBMAT_API submat_status submat_invroot_host(submat_plan_t plan, const double* v
  * no stored iterates) by a cyclic Jacobi with the matrix and eigenvectors held as
  * double-floats (FP32 pairs, ~44 significant bits; the rotation angles, the divided
  * differences and the products with the eigenvectors in FP64).  grad_out and grad_in are
- * device arrays of nnz doubles; grad_in is overwritten.  Returns SUBMAT_ENOFWD if no forward ran on this plan.
+ * device arrays of nnz doubles that must not overlap; grad_in is overwritten.  Returns SUBMAT_ENOFWD if no forward ran on this plan.
  * With opts.grad_deterministic = 1 the per-submatrix gradients G_j of a wave of rows are
  * stored, and each entry (r, c) then adds G_j(r, c) over the wave's rows j whose patterns
  * hold both r and c (the transposed map of the plan: j in R_r and R_c), without atomics.

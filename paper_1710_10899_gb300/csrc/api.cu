@@ -3,7 +3,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -43,6 +45,34 @@ struct GraphEntry {
   double* out = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
+
+// Makes the plan's device current for one call and restores the caller's on every return.
+struct DeviceScope {
+  int prev = 0;
+  bool switched = false;
+  cudaError_t enter(int dev) {
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess || prev == dev) return e;
+    e = cudaSetDevice(dev);
+    switched = e == cudaSuccess;
+    return e;
+  }
+  ~DeviceScope() {
+    if (switched) cudaSetDevice(prev);
+  }
+};
+
+// No C++ exception leaves the C ABI: a failed host allocation becomes SUBMAT_ENOMEM.
+#define SUBMAT_NOTHROW(call)                                       \
+  try {                                                            \
+    return call;                                                   \
+  } catch (const std::bad_alloc&) {                                \
+    return fail(SUBMAT_ENOMEM, "host allocation failed");          \
+  } catch (const std::exception& e_) {                             \
+    return fail(SUBMAT_EINVAL, std::string("host: ") + e_.what()); \
+  } catch (...) {                                                  \
+    return fail(SUBMAT_EINVAL, "host: unknown exception");         \
+  }
 
 }  // namespace
 
@@ -244,8 +274,8 @@ const char* submat_status_string(submat_status s) {
 
 const char* submat_last_error(void) { return g_last_error.c_str(); }
 
-submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* opts,
-                          submat_plan_t* out) {
+static submat_status plan_impl(const submat_csr* csr, int32_t p, const submat_opts* opts,
+                               submat_plan_t* out) {
   g_last_error.clear();
   if (!out) return fail(SUBMAT_EINVAL, "out is NULL");
   *out = nullptr;
@@ -253,6 +283,8 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   if (p < 1) return fail(SUBMAT_EINVAL, "p must be >= 1");
   if (csr->n < 0 || csr->nnz < 0) return fail(SUBMAT_EINVAL, "negative size");
   if (csr->nnz > INT32_MAX) return fail(SUBMAT_EINVAL, "nnz exceeds int32 indexing");
+  if (csr->n > csr->nnz)       // every row stores at least its diagonal entry
+    return fail(SUBMAT_ENODIAG, "fewer stored entries than rows: a row lacks its diagonal");
   if (!csr->rowptr || (csr->nnz > 0 && !csr->colind))
     return fail(SUBMAT_EINVAL, "NULL rowptr/colind");
 
@@ -280,12 +312,12 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
 
   const int32_t n = csr->n;
   const int64_t nnz = csr->nnz;
-  std::vector<int32_t> h_rowptr(n + 1);
+  const size_t rp_bytes = ((size_t)n + 1) * sizeof(int32_t);
+  std::vector<int32_t> h_rowptr((size_t)n + 1);
   if (csr->on_device) {
-    CUDA_TRY(cudaMemcpy(h_rowptr.data(), csr->rowptr, (n + 1) * sizeof(int32_t),
-                        cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(h_rowptr.data(), csr->rowptr, rp_bytes, cudaMemcpyDeviceToHost));
   } else {
-    std::memcpy(h_rowptr.data(), csr->rowptr, (n + 1) * sizeof(int32_t));
+    std::memcpy(h_rowptr.data(), csr->rowptr, rp_bytes);
   }
   if (h_rowptr[0] != 0 || h_rowptr[n] != nnz)
     return fail(SUBMAT_EINVAL, "rowptr[0] must be 0 and rowptr[n] must be nnz");
@@ -304,6 +336,8 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
 
   submat_plan_t P = new (std::nothrow) submat_plan_s();
   if (!P) return fail(SUBMAT_ENOMEM, "host allocation");
+  // released on every early return (and on a host exception); handed out at the end
+  std::unique_ptr<submat_plan_s, void (*)(submat_plan_t)> owner(P, release);
   P->n = n;
   P->nnz = nnz;
   P->p = p;
@@ -312,7 +346,7 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   {
     submat_status sst = submat_shard_rows(n, h_rowptr.data(), o.shard_count, o.shard_rank,
                                           &P->row_begin, &P->row_end);
-    if (sst != SUBMAT_OK) { delete P; return sst; }
+    if (sst != SUBMAT_OK) return sst;
   }
   P->n_jobs = P->row_end - P->row_begin;
   sum_m3 = 0.0;
@@ -321,10 +355,7 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
     sum_m3 += len * len * len;
   }
   P->sum_m3 = sum_m3;
-  auto bail = [&](submat_status st) {
-    release(P);
-    return st;
-  };
+  auto bail = [](submat_status st) { return st; };   // the owner releases P
 #define PLAN_TRY(expr)                                                              \
   do {                                                                              \
     cudaError_t err_ = (expr);                                                      \
@@ -341,7 +372,7 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   PLAN_TRY(set_attr_fp64());
   PLAN_TRY(set_attr_eig());
   const size_t nb = (size_t)(n > 0 ? n : 1);
-  PLAN_TRY(cudaMalloc(&P->d_rowptr, (n + 1) * sizeof(int32_t)));
+  PLAN_TRY(cudaMalloc(&P->d_rowptr, rp_bytes));
   PLAN_TRY(cudaMalloc(&P->d_colind, (nnz > 0 ? nnz : 1) * sizeof(int32_t)));
   PLAN_TRY(cudaMalloc(&P->d_m, nb * sizeof(int32_t)));
   PLAN_TRY(cudaMalloc(&P->d_pos, nb * sizeof(int32_t)));
@@ -352,8 +383,7 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   PLAN_TRY(cudaMalloc(&P->d_ctr_bwd, sizeof(DevCounters)));
   PLAN_TRY(cudaMemset(P->d_ctr, 0, sizeof(DevCounters)));
   PLAN_TRY(cudaMemset(P->d_ctr_bwd, 0, sizeof(DevCounters)));
-  PLAN_TRY(cudaMemcpy(P->d_rowptr, h_rowptr.data(), (n + 1) * sizeof(int32_t),
-                      cudaMemcpyHostToDevice));
+  PLAN_TRY(cudaMemcpy(P->d_rowptr, h_rowptr.data(), rp_bytes, cudaMemcpyHostToDevice));
   if (nnz > 0)
     PLAN_TRY(cudaMemcpy(P->d_colind, csr->colind, nnz * sizeof(int32_t),
                         csr->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
@@ -433,12 +463,12 @@ submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* o
   for (auto& e : P->ev) PLAN_TRY(cudaEventCreate(&e));
   PLAN_TRY(cudaDeviceSynchronize());
 #undef PLAN_TRY
-  *out = P;
+  *out = owner.release();
   return SUBMAT_OK;
 }
 
-submat_status submat_invroot(submat_plan_t P, const double* in, double* out, void* stream,
-                             int32_t sync) {
+static submat_status invroot_impl(submat_plan_t P, const double* in, double* out, void* stream,
+                                  int32_t sync) {
   g_last_error.clear();
   if (!P) return fail(SUBMAT_EINVAL, "plan is NULL");
   if (P->n == 0) return SUBMAT_OK;
@@ -448,9 +478,8 @@ submat_status submat_invroot(submat_plan_t P, const double* in, double* out, voi
   const size_t bytes = (size_t)P->nnz * sizeof(double);
   if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(SUBMAT_EINVAL, "vals_out overlaps vals_in");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  int prev = 0;
-  CUDA_TRY(cudaGetDevice(&prev));
-  if (prev != P->device) CUDA_TRY(cudaSetDevice(P->device));
+  DeviceScope dev;
+  CUDA_TRY(dev.enter(P->device));
   submat_status st = SUBMAT_OK;
   if (P->opts.use_graph) {
     GraphEntry* ge = nullptr;
@@ -494,44 +523,53 @@ submat_status submat_invroot(submat_plan_t P, const double* in, double* out, voi
     if (c.n_notspd > 0)
       return fail(SUBMAT_ENOTSPD, std::to_string(c.n_notspd) + " submatrices not SPD");
   }
-  if (prev != P->device) CUDA_TRY(cudaSetDevice(prev));
   return SUBMAT_OK;
 }
 
-submat_status submat_invroot_host(submat_plan_t P, const double* in, double* out, void* stream) {
+static submat_status invroot_host_impl(submat_plan_t P, const double* in, double* out,
+                                       void* stream) {
   g_last_error.clear();
   if (!P) return fail(SUBMAT_EINVAL, "plan is NULL");
   if (P->n == 0) return SUBMAT_OK;
   if (!in || !out) return fail(SUBMAT_EINVAL, "NULL value array");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)P->nnz * sizeof(double);
+  DeviceScope dev;
+  CUDA_TRY(dev.enter(P->device));
   if (!P->d_host_in) {
     CUDA_TRY(cudaMalloc(&P->d_host_in, bytes));
     CUDA_TRY(cudaMalloc(&P->d_host_out, bytes));
   }
   CUDA_TRY(cudaMemcpyAsync(P->d_host_in, in, bytes, cudaMemcpyHostToDevice, s));
-  submat_status st = submat_invroot(P, P->d_host_in, P->d_host_out, stream, 0);
+  submat_status st = invroot_impl(P, P->d_host_in, P->d_host_out, stream, 0);
   if (st != SUBMAT_OK) return st;
   CUDA_TRY(cudaMemcpyAsync(out, P->d_host_out, bytes, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   DevCounters c;
   CUDA_TRY(cudaMemcpy(&c, P->d_ctr, sizeof(c), cudaMemcpyDeviceToHost));
+  if (c.error) return fail(SUBMAT_ETIMEOUT, "a device pipeline wait timed out");
   if (c.n_notspd > 0)
     return fail(SUBMAT_ENOTSPD, std::to_string(c.n_notspd) + " submatrices not SPD");
   return SUBMAT_OK;
 }
 
-submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, double* grad_in,
-                                      void* stream) {
+static submat_status backward_impl(submat_plan_t P, const double* grad_out, double* grad_in,
+                                   void* stream) {
   g_last_error.clear();
   if (!P) return fail(SUBMAT_EINVAL, "plan is NULL");
   if (!P->have_fwd) return fail(SUBMAT_ENOFWD, "backward before forward");
   if (P->n == 0) return SUBMAT_OK;
   if (!grad_out || !grad_in) return fail(SUBMAT_EINVAL, "NULL gradient array");
+  {
+    const char* a0 = reinterpret_cast<const char*>(grad_out);
+    const char* b0 = reinterpret_cast<const char*>(grad_in);
+    const size_t bytes = (size_t)P->nnz * sizeof(double);
+    if (a0 < b0 + bytes && b0 < a0 + bytes)
+      return fail(SUBMAT_EINVAL, "grad_in overlaps grad_out");
+  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  int prev = 0;
-  CUDA_TRY(cudaGetDevice(&prev));
-  if (prev != P->device) CUDA_TRY(cudaSetDevice(P->device));
+  DeviceScope dev;
+  CUDA_TRY(dev.enter(P->device));
   BwdArgs a{};
   a.rowptr = P->d_rowptr;
   a.colind = P->d_colind;
@@ -556,7 +594,7 @@ submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, d
       // G_j offsets and waves of at most grad_wave_mib MiB
       cudaFree(P->d_gofs);                     // left by an earlier call that ran out of memory
       P->d_gofs = nullptr;
-      std::vector<int64_t> gofs(P->n + 1, 0);
+      std::vector<int64_t> gofs((size_t)P->n + 1, 0);
       for (int32_t j = 0; j < P->n; ++j) gofs[j + 1] = gofs[j] + (int64_t)P->h_m[j] * P->h_m[j];
       const int64_t cap = (int64_t)P->opts.grad_wave_mib * 1024 * 1024 / (int64_t)sizeof(double);
       P->waves.clear();
@@ -568,8 +606,8 @@ submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, d
         wave_max = std::max(wave_max, gofs[j1] - gofs[j0]);
         j0 = j1;
       }
-      CUDA_TRY(cudaMalloc(&P->d_gofs, (P->n + 1) * sizeof(int64_t)));
-      CUDA_TRY(cudaMemcpy(P->d_gofs, gofs.data(), (P->n + 1) * sizeof(int64_t),
+      CUDA_TRY(cudaMalloc(&P->d_gofs, gofs.size() * sizeof(int64_t)));
+      CUDA_TRY(cudaMemcpy(P->d_gofs, gofs.data(), gofs.size() * sizeof(int64_t),
                           cudaMemcpyHostToDevice));
       CUDA_TRY(cudaMalloc(&P->d_gbuf, (size_t)wave_max * sizeof(double)));
     }
@@ -586,13 +624,12 @@ submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, d
     }
   }
   P->last_stream = s;
-  if (prev != P->device) CUDA_TRY(cudaSetDevice(prev));
   return SUBMAT_OK;
 }
 
-submat_status submat_pcg(submat_plan_t P, const double* vals_a, const double* vals_k,
-                         const double* b, double* x, double tol, int32_t max_iter,
-                         int32_t* iters, double* rel_resid, void* stream) {
+static submat_status pcg_impl(submat_plan_t P, const double* vals_a, const double* vals_k,
+                              const double* b, double* x, double tol, int32_t max_iter,
+                              int32_t* iters, double* rel_resid, void* stream) {
   g_last_error.clear();
   if (!P) return fail(SUBMAT_EINVAL, "plan is NULL");
   if (!vals_a || !b || !x) return fail(SUBMAT_EINVAL, "NULL array");
@@ -602,9 +639,8 @@ submat_status submat_pcg(submat_plan_t P, const double* vals_a, const double* va
   if (!(tol > 0.0)) tol = 1e-6;
   if (max_iter <= 0) max_iter = 2 * P->n;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  int prev = 0;
-  CUDA_TRY(cudaGetDevice(&prev));
-  if (prev != P->device) CUDA_TRY(cudaSetDevice(P->device));
+  DeviceScope dev;
+  CUDA_TRY(dev.enter(P->device));
   const int32_t n = P->n;
   const size_t nd = (size_t)n;
   if (!P->d_cg) {
@@ -668,7 +704,6 @@ submat_status submat_pcg(submat_plan_t P, const double* vals_a, const double* va
   if (iters) *iters = it;
   if (rel_resid) *rel_resid = bnorm > 0.0 ? std::sqrt(rr) / bnorm : 0.0;
   P->last_stream = s;
-  if (prev != P->device) CUDA_TRY(cudaSetDevice(prev));
   return st;
 }
 
@@ -718,5 +753,30 @@ submat_status submat_plan_shape(submat_plan_t P, int32_t* n, int64_t* nnz) {
 }
 
 void submat_plan_destroy(submat_plan_t P) { release(P); }
+
+submat_status submat_plan(const submat_csr* csr, int32_t p, const submat_opts* opts,
+                          submat_plan_t* out) {
+  SUBMAT_NOTHROW(plan_impl(csr, p, opts, out))
+}
+
+submat_status submat_invroot(submat_plan_t P, const double* in, double* out, void* stream,
+                             int32_t sync) {
+  SUBMAT_NOTHROW(invroot_impl(P, in, out, stream, sync))
+}
+
+submat_status submat_invroot_host(submat_plan_t P, const double* in, double* out, void* stream) {
+  SUBMAT_NOTHROW(invroot_host_impl(P, in, out, stream))
+}
+
+submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, double* grad_in,
+                                      void* stream) {
+  SUBMAT_NOTHROW(backward_impl(P, grad_out, grad_in, stream))
+}
+
+submat_status submat_pcg(submat_plan_t P, const double* vals_a, const double* vals_k,
+                         const double* b, double* x, double tol, int32_t max_iter,
+                         int32_t* iters, double* rel_resid, void* stream) {
+  SUBMAT_NOTHROW(pcg_impl(P, vals_a, vals_k, b, x, tol, max_iter, iters, rel_resid, stream))
+}
 
 }  // extern "C"

@@ -64,6 +64,7 @@ def test_host_side_validation(lib):
     assert _plan_status(lib, [1, 1], [0]) == "SUBMAT_EINVAL"            # rowptr[0] != 0
     assert _plan_status(lib, [0, 2, 1], [0, 1]) == "SUBMAT_EINVAL"      # decreasing rowptr
     assert _plan_status(lib, [0, 1, 1], [0]) == "SUBMAT_ENODIAG"        # empty row
+    assert _plan_status(lib, [0, 1, 2, 2], [0, 1]) == "SUBMAT_ENODIAG"  # n > nnz
     big = 1537
     assert _plan_status(lib, [0, big], np.arange(big)) == "SUBMAT_ETOOBIG"
     assert lib.submat_plan(None, 2, None, None) != 0
@@ -89,3 +90,24 @@ def test_noalloc_host_side_validation(lib):
     assert pkg.STATUS[lib.submat_invroot_noalloc(4, 4, 1, 1, 0, 8, 1, 1 << 20, None)] == "SUBMAT_EINVAL"
     assert pkg.STATUS[lib.submat_invroot_noalloc(4, 4, 1, 1, 2, 8, 1, 1, None)] == "SUBMAT_EINVAL"
     assert pkg.STATUS[lib.submat_invroot_noalloc(0, 0, None, None, 2, 8, None, None, None)] == "SUBMAT_OK"
+
+
+def test_null_plan_and_arguments(lib):
+    """Every plan-based entry point rejects a NULL plan or NULL arrays with SUBMAT_EINVAL
+    (and a message) before touching the GPU."""
+    import paper_1710_10899_gb300 as pkg
+    buf = (ctypes.c_double * 4)()
+    b = ctypes.addressof(buf)
+
+    def einval(st):
+        return pkg.STATUS[st] == "SUBMAT_EINVAL"
+
+    assert einval(lib.submat_invroot(None, b, b + 16, None, 0))
+    assert einval(lib.submat_invroot_host(None, b, b + 16, None))
+    assert einval(lib.submat_invroot_backward(None, b, b + 16, None))
+    assert einval(lib.submat_pcg(None, b, None, b, b, 0.0, 0, None, None, None))
+    assert einval(lib.submat_get_report(None, None))
+    assert einval(lib.submat_plan_rows(None, None, None))
+    assert einval(lib.submat_plan_shape(None, None, None))
+    assert lib.submat_last_error()
+    lib.submat_plan_destroy(None)                 # a no-op
