@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--oracle-seconds", type=float, default=20.0)
+    ap.add_argument("--oracle-seconds", type=float, default=20.0,
+                    help="single-thread seconds of oracle work per sampled step")
     ap.add_argument("--n", type=int, default=0, help="scale the workload down to n rows")
     return ap.parse_args()
 
@@ -88,10 +89,13 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def time_oracle(a, p, seconds, seed=3):
-    """The oracle as it stands, one single-threaded process per host core, on a row sample
-    sized for about ``seconds`` of CPU work.  Returns (rows/s, cores, sample description).
-    The pool is forked before this process makes any CUDA call."""
+def time_oracle(a, p, seconds, seed=3, steps=1, warmup=0):
+    """The oracle as it stands, one single-threaded process per host core.  Each step is a
+    row sample sized for about ``seconds`` of single-thread CPU work (consecutive slices of
+    one seeded permutation, so the steps take different rows while the matrix has enough);
+    ``warmup`` untimed steps, then ``steps`` timed ones.  Returns (rows/s over the timed
+    steps, cores, sample description).  The pool is forked before this process makes any
+    CUDA call."""
     import multiprocessing as mp
     import numpy as np
     import oracle
@@ -106,19 +110,30 @@ def time_oracle(a, p, seconds, seed=3):
         k0 += 1
     per_row = (time.perf_counter() - t0) / max(k0, 1)
     cores = min(host_cores(), 64)
-    k = int(min(a.n, max(cores, seconds / per_row)))
-    rows = [int(r) for r in perm[:k]]
-    chunks = [rows[i::cores * 4] for i in range(cores * 4)]
-    chunks = [c for c in chunks if c]
+    k = int(min(a.n, max(cores, seconds / per_row)))          # rows per step
+
+    def step_chunks(i):
+        rows = [int(r) for r in perm[(np.arange(k) + i * k) % a.n]]
+        chunks = [rows[c::cores * 4] for c in range(cores * 4)]
+        return rows, [c for c in chunks if c]
+
     _oracle_init(a.rowptr, a.colind, a.vals, p)       # inherited by the forked workers
     ctx = mp.get_context("fork")
+    done, dt, msum = 0, 0.0, 0.0
     with ctx.Pool(cores) as pool:
-        pool.map(_oracle_rows, [[rows[0]]] * cores)          # warm the workers
-        t0 = time.perf_counter()
-        done = sum(pool.map(_oracle_rows, chunks))
-        dt = time.perf_counter() - t0
-    sample = (f"{done} of {a.n} rows (seeded permutation, seed {seed}), "
-              f"mean m {float(m[rows].mean()):.1f}, {dt:.2f} s wall on {cores} processes")
+        pool.map(_oracle_rows, [[int(perm[0])]] * cores)     # start the workers
+        for i in range(warmup):
+            pool.map(_oracle_rows, step_chunks(i)[1])
+        for i in range(warmup, warmup + max(steps, 1)):
+            rows, chunks = step_chunks(i)
+            t0 = time.perf_counter()
+            done += sum(pool.map(_oracle_rows, chunks))
+            dt += time.perf_counter() - t0
+            msum += float(m[rows].sum())
+    nst = max(steps, 1)
+    sample = (f"{nst} timed step(s) after {warmup} untimed, {k} of {a.n} rows each "
+              f"(slices of a seeded permutation, seed {seed}), mean m {msum / done:.1f}, "
+              f"{dt:.2f} s wall on {cores} processes")
     return done / dt, cores, sample
 
 
@@ -222,7 +237,8 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        v, cores, sample = time_oracle(a, p, args.oracle_seconds)
+        v, cores, sample = time_oracle(a, p, args.oracle_seconds, steps=args.steps,
+                                       warmup=args.warmup)
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * a.n / v,
