@@ -425,3 +425,33 @@ def test_refine_newton_dense_fixed_point_and_quadratic_convergence(p):
     assert errs[-1] <= 1e-12
     k = next(i for i, e in enumerate(errs) if e < 1e-3)
     assert errs[k + 1] <= 10 * errs[k] ** 2          # quadratic once close
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_refine_newton_first_order_on_noncommuting_error(p):
+    """Why the refinement from the submatrix result fails (Sec. 4.5 reading): the step
+    X' = ((p+1) X - X (A X^p)) / p, linearised at Z = A^(-1/p) with X = Z + E and E in A's
+    eigenbasis, multiplies E_ab by g(z_b / z_a), g(s) = (p - sum_{k<p} s^k) / p (z = the
+    eigenvalues of Z); the symmetrisation averages g(s) and g(1/s).  Errors within one
+    eigenvalue (s = 1) vanish to first order (quadratic convergence), errors that couple
+    eigenvalues far apart are amplified.  A = diag(1, 100), dense pattern (no truncation):
+    the off-diagonal error of Z + eps E is multiplied by exactly that average (-2.025 for
+    p = 2), the diagonal moves by O(eps^2)."""
+    lam = np.array([1.0, 100.0])
+    z = lam ** (-1.0 / p)
+    rp = np.array([0, 2, 4], dtype=np.int32)
+    ci = np.array([0, 1, 0, 1], dtype=np.int32)
+    av = np.array([1.0, 0.0, 0.0, 100.0])            # stored zeros keep the pattern dense
+    s = z[1] / z[0]
+
+    def g(t):
+        return (p - sum(t ** k for k in range(p))) / p
+
+    expect = 0.5 * (g(s) + g(1.0 / s))
+    assert abs(expect) > 1.0                          # this error component grows
+    for eps in (1e-5, 1e-7):
+        x0 = np.array([z[0], eps, eps, z[1]])
+        x1 = oracle.refine.refine(rp, ci, av, x0, p, 1)[1]
+        assert abs(x1[1] / eps - expect) <= 1e-6 * abs(expect)   # Z's off-diagonal is 0
+        assert x1[1] == x1[2]                         # symmetrised
+        assert max(abs(x1[0] - z[0]), abs(x1[3] - z[1])) <= 100.0 * eps ** 2
