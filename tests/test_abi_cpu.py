@@ -111,3 +111,18 @@ def test_null_plan_and_arguments(lib):
     assert einval(lib.submat_plan_shape(None, None, None))
     assert lib.submat_last_error()
     lib.submat_plan_destroy(None)                 # a no-op
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: without the built library the binding raises ImportError."""
+    import subprocess
+    import sys
+    missing = str(tmp_path / "libsubmat.so")
+    code = ("import paper_1710_10899_gb300 as p\n"
+            "try:\n"
+            f"    p.load_library({missing!r})\n"
+            "except ImportError as e:\n"
+            "    print('raised', e)\n")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                         timeout=120, check=True)
+    assert out.stdout.startswith("raised") and "not found" in out.stdout
