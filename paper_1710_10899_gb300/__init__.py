@@ -301,6 +301,34 @@ def shard_rows(rowptr, count: int, rank: int):
     return int(b.value), int(e.value)
 
 
+def csr_arrays(mat):
+    """(rowptr int32, colind int32, vals float64) of a scipy.sparse matrix (any format), in
+    the form the plan expects: CSR order, column indices ascending and unique within a row
+    (duplicates are summed).  Explicitly stored zeros stay: they are part of the pattern.
+    Host-side conversion only."""
+    import scipy.sparse as sp
+    c = sp.csr_matrix(mat, dtype=np.float64, copy=True)
+    c.sum_duplicates()                      # sorts the indices as well
+    if c.shape[0] != c.shape[1]:
+        raise ValueError(f"expected a square matrix, got {c.shape}")
+    if c.nnz > np.iinfo(np.int32).max:
+        raise ValueError("more than 2^31 - 1 stored entries")
+    return (c.indptr.astype(np.int32), c.indices.astype(np.int32),
+            np.ascontiguousarray(c.data, dtype=np.float64))
+
+
+def scipy_csr(rowptr, colind, vals):
+    """The result values (numpy array or tensor, on any device) on the plan's pattern as a
+    scipy.sparse CSR matrix.  Host-side conversion only."""
+    import scipy.sparse as sp
+    if hasattr(vals, "detach"):             # a torch tensor
+        vals = vals.detach().cpu().numpy()
+    rp = np.asarray(rowptr, dtype=np.int64)
+    n = rp.shape[0] - 1
+    return sp.csr_matrix((np.asarray(vals, dtype=np.float64), np.asarray(colind), rp),
+                         shape=(n, n))
+
+
 SUBMAT_NOALLOC_MAX_M = 1024
 
 
