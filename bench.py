@@ -67,13 +67,16 @@ def dist_env():
 _W = {}
 
 
-def _oracle_init(rowptr, colind, vals, p):
-    _W.update(rowptr=rowptr, colind=colind, vals=vals, p=p)
+def _oracle_init(rowptr, colind, vals, p, route="eig"):
+    _W.update(rowptr=rowptr, colind=colind, vals=vals, p=p, route=route)
 
 
 def _oracle_rows(rows):
     import oracle
-    out = oracle.invroot(_W["rowptr"], _W["colind"], _W["vals"], _W["p"], rows=rows)
+    if _W.get("route") == "lu":        # the paper's p = 1 route: LU inversion per submatrix
+        oracle.invroot_lu(_W["rowptr"], _W["colind"], _W["vals"], rows=rows)
+    else:
+        oracle.invroot(_W["rowptr"], _W["colind"], _W["vals"], _W["p"], rows=rows)
     return len(rows)
 
 
@@ -89,13 +92,14 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def time_oracle(a, p, seconds, seed=3, steps=1, warmup=0):
+def time_oracle(a, p, seconds, seed=3, steps=1, warmup=0, route="eig"):
     """The oracle as it stands, one single-threaded process per host core.  Each step is a
     row sample sized for about ``seconds`` of single-thread CPU work (consecutive slices of
     one seeded permutation, so the steps take different rows while the matrix has enough);
     ``warmup`` untimed steps, then ``steps`` timed ones.  Returns (rows/s over the timed
     steps, cores, sample description).  The pool is forked before this process makes any
-    CUDA call."""
+    CUDA call.  ``route="lu"`` (p = 1 only) times the paper's LU inversion instead of the
+    eigendecomposition."""
     import multiprocessing as mp
     import numpy as np
     import oracle
@@ -106,7 +110,10 @@ def time_oracle(a, p, seconds, seed=3, steps=1, warmup=0):
     t0 = time.perf_counter()
     k0 = 0
     while time.perf_counter() - t0 < 0.5 and k0 < a.n:
-        oracle.row_segment(a.rowptr, a.colind, a.vals, p, int(perm[k0]))
+        if route == "lu":
+            oracle.invroot_lu(a.rowptr, a.colind, a.vals, rows=[int(perm[k0])])
+        else:
+            oracle.row_segment(a.rowptr, a.colind, a.vals, p, int(perm[k0]))
         k0 += 1
     per_row = (time.perf_counter() - t0) / max(k0, 1)
     cores = min(host_cores(), 64)
@@ -117,7 +124,7 @@ def time_oracle(a, p, seconds, seed=3, steps=1, warmup=0):
         chunks = [rows[c::cores * 4] for c in range(cores * 4)]
         return rows, [c for c in chunks if c]
 
-    _oracle_init(a.rowptr, a.colind, a.vals, p)       # inherited by the forked workers
+    _oracle_init(a.rowptr, a.colind, a.vals, p, route)   # inherited by the forked workers
     ctx = mp.get_context("fork")
     done, dt, msum = 0, 0.0, 0.0
     with ctx.Pool(cores) as pool:
@@ -239,6 +246,11 @@ def main():
             return
         v, cores, sample = time_oracle(a, p, args.oracle_seconds, steps=args.steps,
                                        warmup=args.warmup)
+        extra = {}
+        if p == 1:          # the paper's own p = 1 route (LU inversion), reported beside it
+            vl, cl, sl = time_oracle(a, p, args.oracle_seconds, steps=args.steps,
+                                     warmup=args.warmup, route="lu")
+            extra["paper_lu_p1"] = {"value": vl, "unit": UNIT, "cores": cl, "sample": sl}
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * a.n / v,
@@ -247,6 +259,7 @@ def main():
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            **extra,
         }))
         return
 

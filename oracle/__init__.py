@@ -4,7 +4,7 @@ Imported only by ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
 baseline.  It shares no code with the CUDA library in ``paper_1710_10899_gb300``.
 """
 from .submatrix import (  # noqa: F401
-    index_set, plan, submatrix, inv_root, inv_root_column, invroot, row_segment,
+    index_set, plan, submatrix, inv_root, inv_root_column, invroot, invroot_lu, row_segment,
     divided_differences, submatrix_grad, grad, to_dense, residual_2norm,
 )
 from . import cg  # noqa: F401,E402

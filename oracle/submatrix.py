@@ -130,6 +130,27 @@ def row_segment(rowptr, colind, vals, p, j, sign=-1):
 
 
 # ---------------------------------------------------------------------------
+# The paper's own p = 1 route (Sec. 6.1): LU factorisation and inversion per submatrix
+# ---------------------------------------------------------------------------
+
+def invroot_lu(rowptr, colind, vals, rows=None):
+    """The submatrix method for p = 1 computed as in the paper's prototype (Sec. 6.1): each
+    S_j is inverted through its LU factorisation (LAPACK getrf + getri, which
+    ``scipy.linalg.inv`` calls), and Alg. 2 keeps column pos_j of the inverse.  Unlike the
+    spectral route it accepts indefinite nonsingular submatrices (raises on a singular
+    one).  Same result layout as ``invroot``.  Used as the paper-faithful CPU baseline for
+    p = 1; the parity reference stays ``invroot``."""
+    import scipy.linalg as sl
+    nnz = len(colind)
+    out = np.full(nnz, np.nan)
+    n = len(rowptr) - 1
+    for j in (range(n) if rows is None else rows):
+        s, r, pos = submatrix(rowptr, colind, vals, j)
+        out[rowptr[j]:rowptr[j + 1]] = sl.inv(s, check_finite=True)[:, pos]
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Gradient of a loss on the result with respect to A's stored values
 # ---------------------------------------------------------------------------
 

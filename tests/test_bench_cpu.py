@@ -26,3 +26,13 @@ def test_reference_arm_json_line():
     assert e2e["value"] == rec["value"] and e2e["unit"] == rec["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert rec["config"]["workload"].startswith("overlap_uniform(n=1500,")
+
+
+def test_reference_arm_reports_the_paper_lu_route_for_p1():
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+           "--warmup", "0", "--oracle-seconds", "0.3", "--n", "800", "--p", "1"]
+    out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300, check=True)
+    rec = json.loads(out.stdout.strip().splitlines()[-1])
+    lu = rec["paper_lu_p1"]
+    assert lu["value"] > 0 and lu["unit"] == rec["unit"] and lu["cores"] >= 1
+    assert "p=1" in rec["config"]["workload"]

@@ -83,6 +83,28 @@ def test_chain4_p1_exact_rationals():
     np.testing.assert_allclose(y, [float(f) for f in expect], atol=1e-15)
 
 
+def test_paper_lu_route_p1_exact_rationals_and_indefinite():
+    """The paper's own p = 1 route (LU inversion per submatrix, Sec. 6.1): the same exact
+    rationals as the hand-worked chain above, the full inverse with a dense pattern, and an
+    indefinite nonsingular submatrix, which the spectral route rejects and the LU route
+    inverts: A = [[1, 2], [2, 1]], det -3, A^-1 = (1/3) [[-1, 2], [2, -1]]."""
+    a = 2 * np.eye(4) + np.eye(4, k=1) + np.eye(4, k=-1)
+    csr = wl.dense_to_csr(a)
+    y = oracle.invroot_lu(csr.rowptr, csr.colind, csr.vals)
+    expect = [2 / 3, -1 / 3, -1 / 2, 1, -1 / 2, -1 / 2, 1, -1 / 2, -1 / 3, 2 / 3]
+    np.testing.assert_allclose(y, expect, atol=1e-15)
+    d = _dense_spd(20, seed=7)
+    c = wl.dense_to_csr(d, keep=np.ones_like(d, dtype=bool))
+    yd = oracle.to_dense(c.n, c.rowptr, c.colind, oracle.invroot_lu(c.rowptr, c.colind, c.vals))
+    np.testing.assert_allclose(yd, sl.cho_solve(sl.cho_factor(d), np.eye(20)).T, atol=1e-12)
+    ind = np.array([[1.0, 2.0], [2.0, 1.0]])
+    c = wl.dense_to_csr(ind, keep=np.ones((2, 2), dtype=bool))
+    np.testing.assert_allclose(oracle.invroot_lu(c.rowptr, c.colind, c.vals),
+                               [-1 / 3, 2 / 3, 2 / 3, -1 / 3], atol=1e-15)
+    with pytest.raises(ValueError):
+        oracle.invroot(c.rowptr, c.colind, c.vals, 1)
+
+
 def _inv_sqrt_2x2(s):
     # sqrt(S) = (S + sqrt(det) I) / sqrt(tr + 2 sqrt(det)) for 2x2 SPD S
     det = s[0, 0] * s[1, 1] - s[0, 1] * s[1, 0]
