@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=20.0,
                     help="single-thread seconds of oracle work per sampled step")
-    ap.add_argument("--n", type=int, default=0, help="scale the workload down to n rows")
+    ap.add_argument("--n", "--rows", dest="n", type=int, default=0,
+                    help="scale the workload down to n rows (under torchrun use --rows: "
+                         "its launcher takes --n for one of its own options)")
     return ap.parse_args()
 
 

@@ -36,3 +36,22 @@ def test_reference_arm_reports_the_paper_lu_route_for_p1():
     lu = rec["paper_lu_p1"]
     assert lu["value"] > 0 and lu["unit"] == rec["unit"] and lu["cores"] >= 1
     assert "p=1" in rec["config"]["workload"]
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    """Launched like the multi-GPU bench (torchrun, two ranks): rank 0 alone prints one line,
+    the other rank exits 0 without work."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port),
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1",
+           "--warmup", "0", "--oracle-seconds", "0.3", "--rows", "500"]
+    out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300, check=True)
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["impl"] == "reference" and rec["n_gpus"] == 2
+    assert rec["config"]["workload"].startswith("overlap_uniform(n=1000,")   # weak scaling
