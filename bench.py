@@ -316,6 +316,8 @@ def main():
         flops_64 += rep["flops_fp64"]
         fallbacks += rep["n_fallback"]
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clocks = clocks_stop(cproc, cf, local)
     total_ms = sum(ms_steps)
     if world > 1:
