@@ -264,6 +264,24 @@ def test_device_pattern_input(sm):
     np.testing.assert_array_equal(pos, po)
 
 
+def test_host_buffers_match_device_path(sm):
+    """submat_invroot_host (host arrays in and out, copies inside the call) gives the device
+    path's bits, from numpy arrays and from pinned tensors, and meets the bar."""
+    a = wl.overlap_uniform(n=600, kappa=1e3)
+    plan = sm.submat_plan(a.rowptr, a.colind, 2)
+    v = torch.tensor(a.vals, device="cuda")
+    yd = sm.submat_invroot(plan, v, sync=True).cpu().numpy()
+    yh = plan.invroot_host(a.vals)
+    assert np.array_equal(yh, yd)
+    hin = torch.tensor(a.vals).pin_memory()
+    hout = torch.empty(a.nnz, dtype=torch.float64).pin_memory()
+    plan.invroot_host(hin, hout)
+    assert np.array_equal(hout.numpy(), yd)
+    rows = list(range(0, a.n, 5))
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, 2, rows=rows)
+    assert row_errors(a, yh, ref, rows).max() <= TOL["mixed"]
+
+
 def test_invalid_calls(sm):
     a = wl.overlap_small(n=200)
     plan = sm.submat_plan(a.rowptr, a.colind, 2)
