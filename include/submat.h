@@ -127,8 +127,10 @@ typedef struct {
   int64_t n_notspd;        /* rows with a non-positive eigenvalue or non-finite input    */
   double max_resid;        /* largest FP64 column residual seen before the fallback      */
   double sum_m3;           /* sum over rows of m^3 (true sizes)                           */
-  double flops_tensor;     /* tensor-core flops executed by the last forward, counted as
-                              sum_j iters_j * (p+1) * 2 m_j^3 * products (true m_j)      */
+  double flops_tensor;     /* tensor-core flops executed by the last forward: sum over
+                              rows of (GEMMs executed) * 15 FP16 slice products *
+                              2 m_j^3 (true m_j; p GEMMs per iteration for p >= 2;
+                              two for p = 1, plus its final X product)                   */
   double flops_fp64;       /* FP64 flops of the last forward (FP64 path: iterations;
                               mixed path: column refinement; both: fallback)             */
   float ms_kernel;         /* device time of the last forward's main (Newton) kernel,
@@ -200,7 +202,8 @@ SUBMAT_API submat_status submat_invroot_host(submat_plan_t plan, const double* v
  * no stored iterates) by a cyclic Jacobi with the matrix and eigenvectors held as
  * double-floats (FP32 pairs, ~44 significant bits; the rotation angles, the divided
  * differences and the products with the eigenvectors in FP64).  grad_out and grad_in are
- * device arrays of nnz doubles that must not overlap; grad_in is overwritten.  Returns SUBMAT_ENOFWD if no forward ran on this plan.
+ * device arrays of nnz doubles that must not overlap; grad_in is overwritten.  Returns
+ * SUBMAT_ENOFWD if no forward ran on this plan.
  * With opts.grad_deterministic = 1 the per-submatrix gradients G_j of a wave of rows are
  * stored, and each entry (r, c) then adds G_j(r, c) over the wave's rows j whose patterns
  * hold both r and c (the transposed map of the plan: j in R_r and R_c), without atomics.

@@ -126,3 +126,22 @@ def test_missing_library_fails_loudly(tmp_path):
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
                          timeout=120, check=True)
     assert out.stdout.startswith("raised") and "not found" in out.stdout
+
+
+def test_plain_c_caller(lib, tmp_path):
+    """include/submat.h compiles as strict C99, and a C program linked against
+    libsubmat.so runs the host-side entry points (no GPU needed)."""
+    import subprocess
+    import paper_1710_10899_gb300 as pkg
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "abi_check")
+    libdir = os.path.dirname(pkg.LIB_PATH)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_check.c"),
+                    "-o", exe, "-L", libdir, "-lsubmat", "-Wl,-rpath," + libdir],
+                   check=True, capture_output=True, text=True, timeout=120)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    assert "abi_check ok" in out.stdout
