@@ -477,3 +477,36 @@ def test_refine_newton_first_order_on_noncommuting_error(p):
         assert abs(x1[1] / eps - expect) <= 1e-6 * abs(expect)   # Z's off-diagonal is 0
         assert x1[1] == x1[2]                         # symmetrised
         assert max(abs(x1[0] - z[0]), abs(x1[3] - z[1])) <= 100.0 * eps ** 2
+
+
+def _random_symmetric(n, density, seed):
+    rng = np.random.default_rng(seed)
+    mask = np.triu(rng.random((n, n)) < density / 2, 1)
+    v = rng.uniform(-1.0, 1.0, (n, n)) * mask
+    return v + v.T
+
+
+def _shift_to_kappa(off, kappa):
+    lam = np.linalg.eigvalsh(off)
+    return off + (lam[-1] - kappa * lam[0]) / (kappa - 1.0) * np.eye(len(off))
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_sec41_residual_trends(p):
+    """Sec. 4.1's findings, on seeded random sparse SPD matrices (density 0.05, the
+    condition number set by a diagonal shift) instead of MATLAB's sprandsym: the residual
+    ||X^p A - I||_2 grows with the condition number on a fixed pattern, and at kappa = 2 it
+    stays small as n grows."""
+    off = _random_symmetric(200, 0.05, seed=200)
+    res = []
+    for kappa in (2.0, 10.0, 100.0, 1000.0):
+        a = _shift_to_kappa(off, kappa)
+        c = wl.dense_to_csr(a)
+        y = oracle.to_dense(c.n, c.rowptr, c.colind, oracle.invroot(c.rowptr, c.colind, c.vals, p))
+        res.append(oracle.residual_2norm(a, y, p))
+    assert all(r0 < r1 for r0, r1 in zip(res, res[1:])), res
+    for n in (100, 200, 400):
+        a = _shift_to_kappa(_random_symmetric(n, 0.05, seed=n), 2.0)
+        c = wl.dense_to_csr(a)
+        y = oracle.to_dense(c.n, c.rowptr, c.colind, oracle.invroot(c.rowptr, c.colind, c.vals, p))
+        assert oracle.residual_2norm(a, y, p) < 0.15
