@@ -510,3 +510,18 @@ def test_sec41_residual_trends(p):
         c = wl.dense_to_csr(a)
         y = oracle.to_dense(c.n, c.rowptr, c.colind, oracle.invroot(c.rowptr, c.colind, c.vals, p))
         assert oracle.residual_2norm(a, y, p) < 0.15
+
+
+def test_refine_newton_p1_is_indifferent_to_commutation():
+    """For p = 1 the step is Newton-Schulz for the inverse, X' = 2X - X A X: g(s) = 0 for
+    every eigenvalue pair, so an error coupling eigenvalues 100 apart vanishes to first
+    order (the error after the step is O(eps^2)), unlike p >= 2 above."""
+    rp = np.array([0, 2, 4], dtype=np.int32)
+    ci = np.array([0, 1, 0, 1], dtype=np.int32)
+    av = np.array([1.0, 0.0, 0.0, 100.0])
+    z = np.array([1.0, 0.01])
+    for eps in (1e-4, 1e-6):
+        x0 = np.array([z[0], eps, eps, z[1]])
+        x1 = oracle.refine.refine(rp, ci, av, x0, 1, 1)[1]
+        err = np.abs(x1 - np.array([z[0], 0.0, 0.0, z[1]])).max()
+        assert err <= 200.0 * eps ** 2
