@@ -145,3 +145,35 @@ def test_plain_c_caller(lib, tmp_path):
     out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0, out.stderr
     assert "abi_check ok" in out.stdout
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's ctypes structures have the C structs' size and field offsets (a C
+    program built against include/submat.h prints them)."""
+    import subprocess
+    import paper_1710_10899_gb300 as pkg
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"submat_csr": pkg.CSR, "submat_opts": pkg.Opts, "submat_report": pkg.Report}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "submat.h"',
+             "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", exe],
+                   check=True, capture_output=True, text=True, timeout=120)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True, timeout=60).stdout
+    got = {}
+    for ln in out.splitlines():
+        cname, field, val = ln.split()
+        got[(cname, field)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
