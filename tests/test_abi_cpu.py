@@ -177,3 +177,18 @@ def test_ctypes_structs_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
         for field, _ in py._fields_:
             assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def test_binding_constants_match_the_header():
+    """Status codes, precision modes and size limits in the binding are the header's."""
+    import paper_1710_10899_gb300 as pkg
+    text = open(os.path.join(ROOT, "include", "submat.h")).read()
+    enums = {k: int(v) for k, v in re.findall(r"\b(SUBMAT_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    macros = {k: int(v) for k, v in re.findall(r"#define\s+(SUBMAT_[A-Z0-9_]+)\s+(\d+)", text)}
+    status = {k: v for k, v in enums.items() if not k.startswith("SUBMAT_PREC_")}
+    assert {v: k for k, v in status.items()} == pkg.STATUS
+    assert enums["SUBMAT_PREC_FP64"] == pkg.PREC_FP64
+    assert enums["SUBMAT_PREC_MIXED_F16"] == pkg.PREC_MIXED_F16
+    assert enums["SUBMAT_PREC_MIXED_F16_SYNC"] == pkg.PREC_MIXED_F16_SYNC
+    assert macros["SUBMAT_MAX_M"] == pkg.SUBMAT_MAX_M
+    assert macros["SUBMAT_NOALLOC_MAX_M"] == pkg.SUBMAT_NOALLOC_MAX_M
