@@ -192,3 +192,39 @@ def test_binding_constants_match_the_header():
     assert enums["SUBMAT_PREC_MIXED_F16_SYNC"] == pkg.PREC_MIXED_F16_SYNC
     assert macros["SUBMAT_MAX_M"] == pkg.SUBMAT_MAX_M
     assert macros["SUBMAT_NOALLOC_MAX_M"] == pkg.SUBMAT_NOALLOC_MAX_M
+
+
+def _prototypes():
+    text = open(os.path.join(ROOT, "include", "submat.h")).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    out = {}
+    for ret, name, args in re.findall(
+            r"SUBMAT_API\s+([\w\s\*]+?)\s*\b(submat_\w+)\s*\(([^)]*)\)\s*;", text):
+        params = [] if args.strip() in ("", "void") else [a.strip() for a in args.split(",")]
+        out[name] = (" ".join(ret.split()), params)
+    return out
+
+
+def test_ctypes_signatures_match_the_header(lib):
+    """Every argtype / restype of the binding has the width of the header's parameter (a
+    mismatch, e.g. an int where int64_t is expected, would silently corrupt arguments)."""
+    scalars = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double,
+               "submat_status": ctypes.c_int32}
+    protos = _prototypes()
+    assert len(protos) >= 10
+    for name, (ret, params) in protos.items():
+        fn = getattr(lib, name)
+        if ret == "void":
+            assert fn.restype is None, name
+        elif ret == "const char*":
+            assert fn.restype is ctypes.c_char_p, name
+        else:
+            assert fn.restype is scalars[ret], name
+        assert len(fn.argtypes) == len(params), name
+        for decl, at in zip(params, fn.argtypes):
+            ctype = decl.rsplit(None, 1)[0] if not decl.endswith("*") else decl
+            if "*" in decl or ctype.strip() in ("submat_plan_t", "void*"):
+                assert at is ctypes.c_void_p or issubclass(at, ctypes._Pointer), (name, decl)
+            else:
+                base = ctype.replace("const", "").strip()
+                assert at is scalars[base], (name, decl, at)
