@@ -87,3 +87,13 @@ def test_gloo_two_ranks_assemble_the_result(pkg, tmp_path):
     a = wl.overlap_uniform(n=400, kappa=1e3)
     ref = oracle.invroot(a.rowptr, a.colind, a.vals, 2)
     assert np.array_equal(y, ref)
+
+
+def test_more_shards_than_rows_tile_with_empty_shards(pkg):
+    a = wl.overlap_small(n=5)
+    ranges = [pkg.shard_rows(a.rowptr, 8, k) for k in range(8)]
+    assert ranges[0][0] == 0 and ranges[-1][1] == a.n
+    for (b0, e0), (b1, e1) in zip(ranges, ranges[1:]):
+        assert e0 == b1 and b0 <= e0
+    assert sum(e - b for b, e in ranges) == a.n
+    assert any(e == b for b, e in ranges)          # some shards hold no row
