@@ -184,6 +184,7 @@ class Plan:
         self.precision = precision
         self.root_sign = int(root_sign)
         self.device = torch.device("cuda", torch.cuda.current_device())
+        self._fwd_gen = 0              # forwards run on this plan (the backward's input)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -216,6 +217,7 @@ class Plan:
         v = self._vals(vals)
         if out is None:
             out = torch.empty_like(v)
+        self._fwd_gen += 1             # the library saves this call's input for the backward
         _check(self._lib, self._lib.submat_invroot(self._h, ctypes.c_void_p(v.data_ptr()),
                                                    ctypes.c_void_p(out.data_ptr()),
                                                    _stream_ptr(stream), 1 if sync else 0))
@@ -234,6 +236,7 @@ class Plan:
             vals_out = np.empty(self.nnz, dtype=np.float64)
         ptr_out = vals_out.data_ptr() if isinstance(vals_out, torch.Tensor) \
             else vals_out.ctypes.data
+        self._fwd_gen += 1
         _check(self._lib, self._lib.submat_invroot_host(self._h, ctypes.c_void_p(ptr_in),
                                                         ctypes.c_void_p(ptr_out),
                                                         _stream_ptr(stream)))
@@ -366,15 +369,22 @@ def _make_function():
     class SubmatInvRoot(torch.autograd.Function):
         """Autograd wrapper: forward = submat_invroot, backward = submat_invroot_backward.
 
-        The plan keeps the forward input, so nothing is saved on the tape."""
+        The plan keeps the input of its last forward, so nothing is saved on the tape; a
+        backward through an earlier forward of the same plan (whose input is gone) raises
+        instead of returning the gradient at the wrong point."""
 
         @staticmethod
         def forward(ctx, vals, plan):
+            out = plan.invroot(vals)
             ctx.plan = plan
-            return plan.invroot(vals)
+            ctx.fwd_gen = plan._fwd_gen
+            return out
 
         @staticmethod
         def backward(ctx, grad):
+            if ctx.plan._fwd_gen != ctx.fwd_gen:
+                raise RuntimeError("the plan ran another forward after this one; its saved "
+                                   "input is gone (use one plan per differentiated forward)")
             return ctx.plan.backward(grad.contiguous()), None
 
     return SubmatInvRoot
