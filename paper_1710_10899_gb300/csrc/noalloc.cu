@@ -35,12 +35,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 struct NoallocCtrl {
   int32_t queue;       // rows handed out
-  int32_t status;      // bit 1: row longer than m_max or empty, 2: no diagonal, 4: not SPD
+  int32_t status;      // bit 1: row longer than m_max or empty, 2: no diagonal, 4: not SPD,
+                       // 8: an extent or column index out of range
 };
 
 struct NoallocArgs {
   const int32_t* rowptr;
   const int32_t* colind;
+  int64_t nnz;
   int32_t n;
   int32_t p;
   int32_t m_max;
@@ -55,6 +57,32 @@ size_t slot_bytes(int mp) {
   return ((((size_t)mp * mp + 31) / 32) * 32 + 6 * (size_t)mp * mp) * sizeof(double);
 }
 
+// The caller's pattern is not validated by a plan here, so before anything of row j is read
+// beyond rowptr[j..j+1]: its extent [base, base + m) and the extents of the rows named by its
+// column indices must lie in [0, nnz], and those indices in [0, n).  The gather reads nothing
+// else (other rows' column indices are only compared with R_j, never used as addresses).
+// All threads call it; returns the block-wide verdict.
+__device__ bool row_in_bounds(const NoallocArgs& a, int base, int m, int* flag_s) {
+  if (threadIdx.x == 0) *flag_s = 0;
+  __syncthreads();
+  const bool ext_ok = base >= 0 && (int64_t)base + m <= a.nnz;
+  if (ext_ok) {
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+      const int32_t r = a.colind[base + k];
+      bool ok = r >= 0 && r < a.n;
+      if (ok) {
+        const int32_t b = a.rowptr[r], e = a.rowptr[r + 1];
+        ok = b >= 0 && b <= e && (int64_t)e <= a.nnz;
+      }
+      if (!ok) *flag_s = 1;
+    }
+  }
+  __syncthreads();
+  const bool ok = ext_ok && *flag_s == 0;
+  __syncthreads();
+  return ok;
+}
+
 __global__ void __launch_bounds__(kThreads, 1) noalloc_fp64_kernel(NoallocArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* gsm = reinterpret_cast<double*>(smem_raw);              // 2*TK*TB
@@ -65,7 +93,7 @@ __global__ void __launch_bounds__(kThreads, 1) noalloc_fp64_kernel(NoallocArgs a
   double* norm2_s = red_s + kRedDoubles;
   int32_t* R_s = reinterpret_cast<int32_t*>(norm2_s + 2);          // SUBMAT_MAX_M
   int32_t* pair_s = R_s + SUBMAT_MAX_M;                              // SUBMAT_MAX_M
-  __shared__ int job_s, bad_s;
+  __shared__ int job_s, bad_s, oob_s;
   char* scr = a.slots + (size_t)blockIdx.x * a.slot_stride;
   const int tid = threadIdx.x;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
@@ -80,8 +108,17 @@ __global__ void __launch_bounds__(kThreads, 1) noalloc_fp64_kernel(NoallocArgs a
     const int m = a.rowptr[j + 1] - base;
     double* out = a.vals_out + base;
     if (m < 1 || m > a.m_max) {
-      for (int k = tid; k < (m > 0 ? m : 0); k += blockDim.x) out[k] = nan;
+      for (int k = tid; k < (m > 0 ? m : 0); k += blockDim.x)
+        if (base + k >= 0 && (int64_t)base + k < a.nnz) out[k] = nan;
       if (tid == 0) atomicOr(&a.ctrl->status, 1);
+      __syncthreads();
+      continue;
+    }
+    if (!row_in_bounds(a, base, m, &oob_s)) {
+      // the row's own extent may be the bad one: write only inside [0, nnz)
+      for (int k = tid; k < m; k += blockDim.x)
+        if (base + k >= 0 && (int64_t)base + k < a.nnz) out[k] = nan;
+      if (tid == 0) atomicOr(&a.ctrl->status, 8);
       __syncthreads();
       continue;
     }
@@ -256,6 +293,7 @@ extern "C" submat_status submat_invroot_noalloc(int32_t n, int64_t nnz, const in
   NoallocArgs a{};
   a.rowptr = rowptr;
   a.colind = colind;
+  a.nnz = nnz;
   a.n = n;
   a.p = p;
   a.m_max = m_max;
@@ -276,6 +314,8 @@ extern "C" submat_status submat_invroot_noalloc(int32_t n, int64_t nnz, const in
   if (e == cudaSuccess) e = cudaMemcpyAsync(&ctrl, ds.base, sizeof(ctrl), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(SUBMAT_ECUDA, cudaGetErrorString(e));
+  if (ctrl.status & 8)
+    return fail(SUBMAT_EINVAL, "a row extent or column index lies outside [0, nnz] / [0, n)");
   if (ctrl.status & 1) return fail(SUBMAT_ETOOBIG, "a row is empty or longer than m_max");
   if (ctrl.status & 2) return fail(SUBMAT_ENODIAG, "a row does not store its diagonal entry");
   if (ctrl.status & 4) return fail(SUBMAT_ENOTSPD, "a submatrix is not positive definite");
