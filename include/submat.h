@@ -52,7 +52,17 @@ typedef enum {
 /* Largest submatrix order (row length) the library accepts. */
 #define SUBMAT_MAX_M 1536
 
-/* Precision of the submatrix operation. */
+/*
+ * Precision of the submatrix operation.  The iteration's products run on FP16 tensor cores
+ * rather than as single TF32 or BF16 products: rounding errors made in any step of the
+ * coupled iteration stay in its limit (X_inf = X_k M_k^(-1/p) from any iterate on), so a
+ * low-precision phase followed by FP64 refinement leaves ~1e-3 (TF32) or ~1e-2 (BF16) for
+ * p >= 2, and the tensor cores' FP32 accumulation truncates.  Each matrix is therefore split
+ * into five FP16 planes of small integers whose level sums the FP32 accumulators hold
+ * exactly (an error-free splitting in the manner of Ozaki et al.), ~39 significant bits;
+ * FP64 stays for the gather, the scaling, the column output and its residual, the p = 1
+ * refinement and the eigendecomposition fallback.
+ */
 enum {
   SUBMAT_PREC_FP64 = 0,       /* coupled Newton iteration entirely in FP64 (CUDA cores)     */
   SUBMAT_PREC_MIXED_F16 = 1,  /* coupled Newton iteration on the tensor cores (tcgen05) with
@@ -137,6 +147,11 @@ typedef struct {
                               from CUDA events recorded around it on the launch stream   */
   float ms_fallback;       /* device time of the last forward's fallback kernel          */
   int64_t n_illcond;       /* rows sent to the fallback by the condition estimate        */
+  double flops_alg;        /* the method's flops of the last forward, independent of the
+                              engine: sum over rows of k_j (p+1) 2 m_j^3 with the executed
+                              iteration count k_j and the true order m_j, every product
+                              counted as a dense GEMM (p = 1 adds 2 m_j^3 for its final X
+                              product); divide by ms_kernel for the roofline rate        */
 } submat_report;
 
 typedef struct submat_plan_s* submat_plan_t;
@@ -238,6 +253,17 @@ SUBMAT_API submat_status submat_get_report(submat_plan_t plan, submat_report* ou
  */
 SUBMAT_API submat_status submat_plan_rows(submat_plan_t plan, int32_t* m, int32_t* pos);
 
+/*
+ * Test aid for the bounded device waits (the paper has no counterpart).  While on != 0,
+ * every CTA of the plan's tensor-core forward (SUBMAT_PREC_MIXED_F16) first waits on a
+ * pipeline barrier that nothing signals, before it issues any copy or tensor-core operation;
+ * the wait gives up after its poll limit (on the order of a second), the CTA writes NaN to
+ * every row it takes from the work queue, and submat_invroot returns SUBMAT_ETIMEOUT (with
+ * sync != 0; submat_get_report still works).  on = 0 restores normal operation.  Other
+ * precisions ignore the flag.  Synchronises the device.
+ */
+SUBMAT_API submat_status submat_test_stall(submat_plan_t plan, int32_t on);
+
 /* Order n and entry count nnz of the plan's pattern. */
 SUBMAT_API submat_status submat_plan_shape(submat_plan_t plan, int32_t* n, int64_t* nnz);
 
@@ -254,13 +280,18 @@ SUBMAT_API submat_status submat_plan_shape(submat_plan_t plan, int32_t* n, int64
  * that loads the library holds until the process exits.
  *
  *   n, nnz, rowptr, colind  A's pattern in device memory (sorted, unique, symmetric, every
- *                           diagonal stored; not re-checked here, see submat_plan)
+ *                           diagonal stored).  Before touching a row's data the kernel checks
+ *                           that the row's extent and the extents of the rows its column
+ *                           indices name lie in [0, nnz] and that those indices lie in
+ *                           [0, n); a row that fails gets NaN and the call SUBMAT_EINVAL.
+ *                           Sortedness and symmetry are not re-checked (see submat_plan)
  *   p                       root order, >= 1
  *   m_max                   the caller's bound on the row lengths, 1..SUBMAT_NOALLOC_MAX_M;
  *                           larger values return SUBMAT_ETOOBIG before any GPU work, and a
  *                           row longer than m_max (or empty) gets NaN and SUBMAT_ETOOBIG
  *   vals_in, vals_out       device arrays of nnz doubles, not overlapping
- *   stream                  cudaStream_t; the call is synchronous (it waits for the stream)
+ *   stream                  cudaStream_t; the call is synchronous: it waits for the stream
+ *                           and reads a status word back before it returns
  *
  * Returns SUBMAT_ENODIAG / SUBMAT_ENOTSPD as the plan-based calls do (affected rows NaN).
  * The first call on a device looks up the array's device address and sets the kernel's

@@ -62,7 +62,7 @@ class Report(ctypes.Structure):
                 ("max_resid", ctypes.c_double), ("sum_m3", ctypes.c_double),
                 ("flops_tensor", ctypes.c_double), ("flops_fp64", ctypes.c_double),
                 ("ms_kernel", ctypes.c_float), ("ms_fallback", ctypes.c_float),
-                ("n_illcond", ctypes.c_int64)]
+                ("n_illcond", ctypes.c_int64), ("flops_alg", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -72,7 +72,7 @@ EXPORTS = ["submat_default_opts", "submat_plan", "submat_invroot", "submat_invro
            "submat_invroot_backward",
            "submat_get_report", "submat_plan_rows", "submat_plan_shape", "submat_plan_destroy",
            "submat_status_string", "submat_last_error", "submat_invroot_noalloc", "submat_pcg",
-           "submat_shard_rows"]
+           "submat_shard_rows", "submat_test_stall"]
 
 _lib_handle = None
 
@@ -115,6 +115,8 @@ def load_library(path: str = LIB_PATH):
     lib.submat_pcg.restype = i32
     lib.submat_shard_rows.argtypes = [i32, vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.submat_shard_rows.restype = i32
+    lib.submat_test_stall.argtypes = [vp, i32]
+    lib.submat_test_stall.restype = i32
     _lib_handle = lib
     return lib
 
@@ -198,6 +200,11 @@ class Plan:
         pos = np.zeros(self.n, dtype=np.int32)
         _check(self._lib, self._lib.submat_plan_rows(self._h, m.ctypes.data, pos.ctypes.data))
         return m, pos
+
+    def test_stall(self, on: bool):
+        """``submat_test_stall``: make the tensor-core forward's first pipeline wait run out
+        (test aid for the bounded device waits; the forward then returns SUBMAT_ETIMEOUT)."""
+        _check(self._lib, self._lib.submat_test_stall(self._h, 1 if on else 0))
 
     def report(self) -> dict:
         r = Report()

@@ -96,6 +96,7 @@ struct submat_plan_s {
   int32_t* d_order = nullptr;
   int32_t* d_fallback = nullptr;
   int32_t* d_flags = nullptr;
+  int32_t* d_stall = nullptr;         // submat_test_stall's flag, read by the tcgen05 forward
   DevCounters* d_ctr = nullptr;       // forward counters
   DevCounters* d_ctr_bwd = nullptr;   // backward counters
   char* d_scratch = nullptr;
@@ -148,6 +149,7 @@ void release(submat_plan_t P) {
   cudaFree(P->d_order);
   cudaFree(P->d_fallback);
   cudaFree(P->d_flags);
+  cudaFree(P->d_stall);
   cudaFree(P->d_ctr);
   cudaFree(P->d_ctr_bwd);
   cudaFree(P->d_scratch);
@@ -193,6 +195,7 @@ submat_status enqueue_forward(submat_plan_t P, const double* in, double* out, cu
   a.engine = P->opts.precision == SUBMAT_PREC_MIXED_F16_SYNC ? 1 : 0;
   a.tm_a = P->tm_a;
   a.tm_b = P->tm_b;
+  a.stall = P->d_stall;
   CUDA_TRY(cudaMemcpyAsync(P->d_saved, in, (size_t)P->nnz * sizeof(double),
                            cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemsetAsync(P->d_ctr, 0, sizeof(DevCounters), s));
@@ -379,6 +382,8 @@ static submat_status plan_impl(const submat_csr* csr, int32_t p, const submat_op
   PLAN_TRY(cudaMalloc(&P->d_order, nb * sizeof(int32_t)));
   PLAN_TRY(cudaMalloc(&P->d_fallback, nb * sizeof(int32_t)));
   PLAN_TRY(cudaMalloc(&P->d_flags, sizeof(int32_t)));
+  PLAN_TRY(cudaMalloc(&P->d_stall, sizeof(int32_t)));
+  PLAN_TRY(cudaMemset(P->d_stall, 0, sizeof(int32_t)));
   PLAN_TRY(cudaMalloc(&P->d_ctr, sizeof(DevCounters)));
   PLAN_TRY(cudaMalloc(&P->d_ctr_bwd, sizeof(DevCounters)));
   PLAN_TRY(cudaMemset(P->d_ctr, 0, sizeof(DevCounters)));
@@ -729,6 +734,7 @@ submat_status submat_get_report(submat_plan_t P, submat_report* r) {
   r->flops_tensor = c.flops_tensor;
   r->flops_fp64 = c.flops_fp64;
   r->n_illcond = (int64_t)c.n_illcond;
+  r->flops_alg = c.flops_alg;
   if (P->have_fwd) {
     CUDA_TRY(cudaEventElapsedTime(&r->ms_kernel, P->ev[0], P->ev[1]));
     CUDA_TRY(cudaEventElapsedTime(&r->ms_fallback, P->ev[1], P->ev[2]));
@@ -742,6 +748,17 @@ submat_status submat_plan_rows(submat_plan_t P, int32_t* m, int32_t* pos) {
   if (P->n == 0) return SUBMAT_OK;
   CUDA_TRY(cudaMemcpy(m, P->d_m, P->n * sizeof(int32_t), cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemcpy(pos, P->d_pos, P->n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return SUBMAT_OK;
+}
+
+submat_status submat_test_stall(submat_plan_t P, int32_t on) {
+  g_last_error.clear();
+  if (!P) return fail(SUBMAT_EINVAL, "plan is NULL");
+  DeviceScope dev;
+  CUDA_TRY(dev.enter(P->device));
+  const int32_t v = on != 0 ? 1 : 0;
+  CUDA_TRY(cudaDeviceSynchronize());          // no forward of this plan reads the flag now
+  CUDA_TRY(cudaMemcpy(P->d_stall, &v, sizeof(v), cudaMemcpyHostToDevice));
   return SUBMAT_OK;
 }
 

@@ -30,6 +30,9 @@ struct DevCounters {
   double flops_tensor;
   unsigned long long n_illcond;        // rows sent to the fallback by the condition estimate
   int32_t error;                       // a device pipeline wait timed out
+  double flops_alg;                    // sum over rows of k_j (p+1) 2 m_j^3 (+ 2 m_j^3 for
+                                       // p = 1's final X product): executed iterations k_j,
+                                       // true orders m_j, every product counted as a dense GEMM
 };
 
 // Arguments of the forward kernels.
@@ -57,6 +60,9 @@ struct FwdArgs {
   int32_t refine_steps;
   double kappa_max;
   int32_t sign;              // -1: A^(-1/p), +1: A^(1/p)
+  const int32_t* stall;      // tcgen05 engine: nonzero makes every CTA first wait on a barrier
+                             // that nothing signals (exercises the bounded wait; see
+                             // submat_test_stall)
 };
 
 struct BwdArgs {

@@ -177,6 +177,8 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_fp64_kernel(FwdArgs a) {
       const double n_gemm = track ? (double)iters * p : (double)iters * 2.0;   // + final X (p = 1)
       atomicAdd(&a.ctr->flops_fp64,
                 n_gemm * 2.0 * m3 + refine_flops(m, p, a.refine_steps));
+      // the method's own count: (p+1) dense products per iteration (+ p = 1's final one)
+      atomicAdd(&a.ctr->flops_alg, ((double)iters * (p + 1) + (p == 1 ? 1.0 : 0.0)) * 2.0 * m3);
     }
     __syncthreads();
   }

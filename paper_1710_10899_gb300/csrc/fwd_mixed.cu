@@ -1061,13 +1061,29 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     if (tid == 0) *abort_s = 0;
     __syncthreads();
   }
+  if (TC && a.stall != nullptr && *a.stall != 0) {
+    // test aid (submat_test_stall): wait on a barrier that nothing signals, before any copy
+    // or tensor-core operation is issued, so the bounded wait gives up and the CTA unwinds
+    uint64_t* never = bars + 2 * TC_STAGES + 2;
+    if (tid == 0) {
+      tc::mbar_init(never, 1);
+      tc::fence_mbar_init();
+      if (!tc::mbar_wait(never, 0, TC_WAIT_LIMIT)) *abort_s = 1;
+    }
+    __syncthreads();
+  }
 
+  int pending = -1;          // a row taken from the queue and left unfinished by a time-out
   for (;;) {
     if (tid == 0) job_s = atomicAdd(&a.ctr->queue, 1);
     __syncthreads();
     const int idx = job_s;
     __syncthreads();
-    if (idx >= a.n || *abort_s) break;
+    if (idx >= a.n) break;
+    if (*abort_s) {
+      pending = a.order[idx];
+      break;
+    }
     const int j = a.order[idx];
     const int m = a.m[j];
     const int pos = a.pos[j];
@@ -1261,7 +1277,10 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
       if (st.newton && nrm2 <= stag2 && nrm2 > 0.25f * prev2) break;
       prev2 = nrm2;
     }
-    if (stop) break;
+    if (stop) {
+      pending = j;
+      break;
+    }
 
     // last step.  p >= 2: X_K M_K^(-1/p) is the limit (M_K = X_K^p M_0, all commuting), so
     // the carried column takes M_K^(-1/p) = (I - E)^(-1/p), E = I - M_K, as its Taylor
@@ -1312,7 +1331,10 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
       X[xc ^ 1].e = exp_of(xmax * 2.f) + eb;
       if (tid == 0) *amax_s = 0u;
       __syncthreads();
-      if (!gemm(X[xc], B3[mi], X[xc ^ 1], X[xc], EPI_AMAX, nullptr)) break;
+      if (!gemm(X[xc], B3[mi], X[xc ^ 1], X[xc], EPI_AMAX, nullptr)) {
+        pending = j;
+        break;
+      }
       ++n_gemm;
       xc ^= 1;
       SliceLoad xl{X[xc].q, plane, LD, ldexp(1.0, X[xc].e - 7)};
@@ -1344,12 +1366,34 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
       atomicAdd(&a.ctr->flops_fp64, refine_flops(m, p, a.refine_steps));
       // fifteen FP16 slice products per GEMM, counted with the true order m
       atomicAdd(&a.ctr->flops_tensor, (double)n_gemm * 15.0 * 2.0 * (double)m * m * m);
+      // the method's own count: (p+1) dense products of order m per iteration (+ p = 1's
+      // final X product), whatever this engine executes for them
+      atomicAdd(&a.ctr->flops_alg,
+                ((double)iters * (p + 1) + (p == 1 ? 1.0 : 0.0)) * 2.0 * (double)m * m * m);
     }
     __syncthreads();
   }
 
   __syncthreads();
-  if (*abort_s && tid == 0) atomicExch(&a.ctr->error, 1);
+  if (*abort_s) {
+    // a pipeline wait gave up: the row this CTA left unfinished and every row it takes from
+    // the queue from now on are written as NaN (plain stores; nothing else is issued)
+    if (tid == 0) atomicExch(&a.ctr->error, 1);
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int j = pending;;) {
+      if (j >= 0) {
+        double* out = a.vals_out + a.rowptr[j];
+        for (int k = tid; k < a.m[j]; k += blockDim.x) out[k] = nan;
+      }
+      __syncthreads();
+      if (tid == 0) job_s = atomicAdd(&a.ctr->queue, 1);
+      __syncthreads();
+      const int idx = job_s;
+      __syncthreads();
+      if (idx >= a.n) break;
+      j = a.order[idx];
+    }
+  }
   if (TC) {
     tc::tc_fence_before();
     __syncthreads();

@@ -122,6 +122,28 @@ def test_edge_patterns(sm, precision):
             assert err.max() <= TOL[precision], (a.name, p, err.max())
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("p", [1, 2])
+def test_algorithmic_flop_count(sm, precision, p):
+    """flops_alg counts (p+1) dense products of the true order per executed iteration, plus
+    p = 1's final X product: with every row of one order m (dense 40 x 40 blocks) it is
+    (p+1) 2 m^3 iters_sum (+ 2 m^3 per row for p = 1)."""
+    import scipy.linalg as sl
+    rng = np.random.default_rng(31)
+    blocks = []
+    for _ in range(12):
+        q = rng.standard_normal((40, 40))
+        blocks.append(q @ q.T / 40 + 0.5 * np.eye(40))
+    a = wl.dense_to_csr(sl.block_diag(*blocks),
+                        keep=sl.block_diag(*[np.ones((40, 40), bool)] * 12))
+    plan, y = run(sm, a, p, precision)
+    rep = plan.report()
+    m3 = 40.0 ** 3
+    expect = (p + 1) * 2 * m3 * rep["iters_sum"] + (2 * m3 * a.n if p == 1 else 0.0)
+    assert rep["iters_sum"] > 0
+    assert rep["flops_alg"] == pytest.approx(expect, rel=1e-12)
+
+
 def test_dense_pattern_equals_full_root(sm):
     import scipy.linalg as sl
     rng = np.random.default_rng(9)
