@@ -9,3 +9,4 @@ from .submatrix import (  # noqa: F401
 )
 from . import cg  # noqa: F401,E402
 from . import refine  # noqa: F401,E402
+from . import pool  # noqa: F401,E402

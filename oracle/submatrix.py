@@ -184,15 +184,17 @@ def submatrix_grad(s, pos, g, p, sign=-1):
     return v @ (gam * (v.T @ gbar @ v)) @ v.T
 
 
-def grad(rowptr, colind, vals, p, grad_out, sign=-1):
+def grad(rowptr, colind, vals, p, grad_out, sign=-1, rows=None):
     """Gradient of L = sum(grad_out * invroot(A, sign)) with respect to A's stored values.
 
     For every row j: G_j = dL/dS_j (``submatrix_grad``), then G_j[k][l] is added to the
     stored value at (R_j[k], R_j[l]).  Entries of S_j that are not stored in A are
-    constants (zero) and receive nothing."""
+    constants (zero) and receive nothing.  L is a sum over rows (each row's segment depends
+    on S_j alone), so with ``rows`` given the result is the contribution of those rows'
+    terms; contributions of disjoint row sets add up to the full gradient."""
     n = len(rowptr) - 1
     out = np.zeros(len(colind))
-    for j in range(n):
+    for j in (range(n) if rows is None else rows):
         s, r, pos = submatrix(rowptr, colind, vals, j)
         gj = submatrix_grad(s, pos, np.asarray(grad_out[rowptr[j]:rowptr[j + 1]]), p, sign)
         for k in range(len(r)):

@@ -38,6 +38,9 @@ rescaled so the expected number of neighbours stays the same.
 from __future__ import annotations
 
 import dataclasses
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as sla
@@ -88,17 +91,42 @@ def _pairs(points, cutoff, box=None):
     return pairs, np.exp(-r2 / GAUSS_WIDTH)
 
 
+def _row_split_operator(m: sp.csr_matrix):
+    """x -> m x as a LinearOperator whose product runs over row blocks in threads.  Each
+    row's sum is formed exactly as in ``m @ x``, so the result (and every Lanczos run built
+    on it) is bit-identical to the single-threaded product."""
+    n = m.shape[0]
+    k = max(1, min(16, os.cpu_count() or 1, n // 4096))
+    bounds = np.linspace(0, n, k + 1).astype(np.int64)
+    parts = [m[bounds[i]:bounds[i + 1]] for i in range(k)]
+    pool = ThreadPoolExecutor(k)
+
+    def mv(x):
+        x = np.asarray(x, dtype=np.float64).ravel()
+        return np.concatenate(list(pool.map(lambda part: part @ x, parts)))
+
+    return sla.LinearOperator((n, n), matvec=mv, dtype=np.float64), pool
+
+
+def _extreme_eig_pair(m: sp.csr_matrix, seed: int):
+    """Largest and smallest eigenvalue of the symmetric m (ARPACK Lanczos, seeded start);
+    the smallest via the largest of (hi I - m), which Lanczos separates better."""
+    v0 = np.random.default_rng(seed).standard_normal(m.shape[0])
+    op, pool = _row_split_operator(m)
+    hi = sla.eigsh(op, k=1, which="LA", v0=v0, tol=1e-8, return_eigenvectors=False)[0]
+    pool.shutdown()
+    op, pool = _row_split_operator((hi * sp.identity(m.shape[0], format="csr") - m).tocsr())
+    lo = hi - sla.eigsh(op, k=1, which="LA", v0=v0, tol=1e-8, return_eigenvectors=False)[0]
+    pool.shutdown()
+    return float(lo), float(hi)
+
+
 def _extreme_eigs(n, pairs, offvals, seed=0):
     """Extreme eigenvalues of the zero-diagonal part (ARPACK Lanczos, seeded start)."""
     i = np.concatenate([pairs[:, 0], pairs[:, 1]])
     j = np.concatenate([pairs[:, 1], pairs[:, 0]])
     off = sp.csr_matrix((np.concatenate([offvals, offvals]), (i, j)), shape=(n, n))
-    v0 = np.random.default_rng(seed).standard_normal(n)
-    hi = sla.eigsh(off, k=1, which="LA", v0=v0, tol=1e-8, return_eigenvectors=False)[0]
-    # smallest eigenvalue via the largest of (hi*I - off), better separated for Lanczos
-    lo = hi - sla.eigsh(hi * sp.identity(n, format="csr") - off, k=1, which="LA", v0=v0,
-                        tol=1e-8, return_eigenvectors=False)[0]
-    return float(lo), float(hi)
+    return _extreme_eig_pair(off, seed)
 
 
 def diag_for_kappa(lo: float, hi: float, kappa: float) -> float:
@@ -195,6 +223,23 @@ def random_on_pattern(a: CSR, seed: int, symmetric: bool = False) -> np.ndarray:
     return w
 
 
+def stratified_rows(m: np.ndarray, k: int, seed: int = 3) -> np.ndarray:
+    """A seeded sample of about k row indices stratified by row size: the sizes are binned
+    by powers of two (below 32, 32..63, ..., 1024..2047, 2048 and above), each non-empty bin
+    gives an equal share (all its rows if it has fewer), and the rows of the smallest and
+    the largest size are always included.  Sorted, unique."""
+    m = np.asarray(m)
+    rng = np.random.default_rng(seed)
+    edges = [0, 32, 64, 128, 256, 512, 1024, 2048, np.iinfo(np.int64).max]
+    bins = [np.nonzero((m >= lo) & (m < hi))[0] for lo, hi in zip(edges[:-1], edges[1:])]
+    bins = [b for b in bins if len(b)]
+    share = max(1, k // max(1, len(bins)))
+    pick = [np.nonzero(m == m.min())[0][:1], np.nonzero(m == m.max())[0][:1]]
+    for b in bins:
+        pick.append(b if len(b) <= share else rng.choice(b, size=share, replace=False))
+    return np.unique(np.concatenate(pick)).astype(np.int64)
+
+
 def block_overlap(atoms: int = 20000, funcs: int = 13, seed: int = 0,
                   kappa: float = 1e4) -> CSR:
     """Block-sparse Gaussian-basis overlap matrix (n = atoms * funcs), see the module doc."""
@@ -226,11 +271,8 @@ def block_overlap(atoms: int = 20000, funcs: int = 13, seed: int = 0,
     v = np.concatenate([blk.ravel(), blk.ravel(), np.broadcast_to(pref, (atoms, funcs, funcs)).ravel()])
     g = sp.csr_matrix((v, (i, j)), shape=(n, n))
     g.sum_duplicates()
-    v0 = np.random.default_rng(seed).standard_normal(n)
-    hi = sla.eigsh(g, k=1, which="LA", v0=v0, tol=1e-8, return_eigenvectors=False)[0]
-    lo = hi - sla.eigsh(hi * sp.identity(n, format="csr") - g, k=1, which="LA", v0=v0,
-                        tol=1e-8, return_eigenvectors=False)[0]
-    g = (g + diag_for_kappa(float(lo), float(hi), kappa) * sp.identity(n, format="csr")).tocsr()
+    lo, hi = _extreme_eig_pair(g, seed)
+    g = (g + diag_for_kappa(lo, hi, kappa) * sp.identity(n, format="csr")).tocsr()
     g.sort_indices()
     return CSR(n, g.indptr.astype(np.int32), g.indices.astype(np.int32),
                g.data.astype(np.float64), f"block_overlap(atoms={atoms},funcs={funcs},kappa={kappa:g})")
