@@ -6,8 +6,23 @@ Default workload: the uniform 3-D overlap matrix, n=32768 (m_j 32..255), kappa ~
 mixed precision.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload overlap_uniform|overlap_small|overlap_clustered|overlap_grad]
-                    [--p P] [--precision mixed|fp64] [--no-fp64-compare]
+                    [--workload overlap_uniform|overlap_small|overlap_clustered|overlap_grad|
+                                block_overlap] [--p P] [--precision mixed|fp64]
+                    [--no-fp64-compare] [--no-extras] [--extras a,b,...]
+
+The line carries, besides the contract's keys:
+  * the accuracy of every row of the result against the FP64 oracle (computed on the host
+    cores before the GPU work starts; its wall time is the CPU baseline);
+  * ``roofline``: the method's flops (sum over rows of k_j (p+1) 2 m_j^3, executed iteration
+    counts, true orders) per launch of the dominant kernel over its CUDA-event time, against
+    the measured dense BF16 (= FP16) rate; the tensor-core work the engine executes for them
+    (15 FP16 slice products per product) is reported beside it as
+    ``executed_tensor_tflops``;
+  * ``fp64_path``: the all-FP64 GPU path on the same input (median of --fp64-steps steps)
+    and its error against the oracle on every row;
+  * ``extras``: the other workloads (p = 1 and 3, the positive root, the small FP64
+    workload, the clustered and the block-sparse workloads, the adjoint), each timed and
+    checked against the oracle (every row, or a seeded sample stratified by row size).
 
 With N > 1 (torchrun) the workload is built N times larger (same recipe, n x N rows) and
 its rows are sharded across ranks (Sec. 6.1.1: every rank holds the whole matrix and
@@ -25,8 +40,8 @@ import subprocess
 import sys
 import time
 
-# The oracle baseline runs one single-threaded process per core: pin the BLAS pools to one
-# thread before numpy is first imported (the workers are forked from this process).
+# The oracle runs in single-threaded worker processes forked from this one: pin the BLAS
+# pools to one thread before numpy is first imported.
 for _k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ[_k] = "1"
 
@@ -36,6 +51,21 @@ sys.path.insert(0, ROOT)
 METRIC = "submatrices/s & TFLOP/s for sparse A^(-1/p) at rel.err<=1e-6 vs FP64 path, % peak"
 UNIT = "submatrices/s"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
+FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (CUDA cores), nominal
+DTYPE_MIXED = "f16x5-slices/f32acc-per-level+f64"
+
+# The extra workloads of the default run: (name, workload, p, precision, root sign, rows
+# checked against the oracle (0 = every row), warm-up steps, timed steps).
+EXTRAS = [
+    ("uniform_p1", "overlap_uniform", 1, "mixed", -1, 1024, 3, 5),
+    ("uniform_p3", "overlap_uniform", 3, "mixed", -1, 1024, 3, 5),
+    ("uniform_p2_positive_root", "overlap_uniform", 2, "mixed", +1, 1024, 3, 5),
+    ("small_fp64", "overlap_small", 2, "fp64", -1, 0, 3, 5),
+    ("small_mixed", "overlap_small", 2, "mixed", -1, 0, 3, 5),
+    ("clustered", "overlap_clustered", 2, "mixed", -1, 512, 1, 3),
+    ("block", "block_overlap", 2, "mixed", -1, 128, 1, 1),
+    ("backward", "overlap_grad", 2, "mixed", -1, 0, 1, 3),
+]
 
 
 def parse():
@@ -48,8 +78,12 @@ def parse():
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--extras", default="",
+                    help="comma-separated subset of the extra workloads (default: all)")
     ap.add_argument("--oracle-seconds", type=float, default=20.0,
-                    help="single-thread seconds of oracle work per sampled step")
+                    help="reference arm: single-thread seconds of oracle work per step")
     ap.add_argument("--n", "--rows", dest="n", type=int, default=0,
                     help="scale the workload down to n rows (under torchrun use --rows: "
                          "its launcher takes --n for one of its own options)")
@@ -63,8 +97,20 @@ def dist_env():
     return rank, world, local
 
 
+def log(msg):
+    sys.stderr.write(f"[bench {time.strftime('%H:%M:%S')}] {msg}\n")
+    sys.stderr.flush()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 # ----------------------------------------------------------------------------------------
-# oracle timing (CPU baseline / reference arm)
+# oracle (CPU baseline, accuracy reference, reference arm); run before any CUDA call
 # ----------------------------------------------------------------------------------------
 _W = {}
 
@@ -82,36 +128,21 @@ def _oracle_rows(rows):
     return len(rows)
 
 
-def log(msg):
-    sys.stderr.write(f"[bench {time.strftime('%H:%M:%S')}] {msg}\n")
-    sys.stderr.flush()
-
-
-def host_cores():
-    try:
-        return len(os.sched_getaffinity(0))
-    except Exception:
-        return os.cpu_count() or 1
-
-
-def time_oracle(a, p, seconds, seed=3, steps=1, warmup=0, route="eig"):
-    """The oracle as it stands, one single-threaded process per host core.  Each step is a
-    row sample sized for about ``seconds`` of single-thread CPU work (consecutive slices of
-    one seeded permutation, so the steps take different rows while the matrix has enough);
-    ``warmup`` untimed steps, then ``steps`` timed ones.  Returns (rows/s over the timed
-    steps, cores, sample description).  The pool is forked before this process makes any
-    CUDA call.  ``route="lu"`` (p = 1 only) times the paper's LU inversion instead of the
-    eigendecomposition."""
+def time_oracle_sampled(a, p, seconds, seed=3, steps=1, warmup=0, route="eig"):
+    """The reference arm: the oracle as it stands, one single-threaded process per host core.
+    Each step is a row sample sized for about ``seconds`` of single-thread CPU work
+    (consecutive slices of one seeded permutation); ``warmup`` untimed steps, then ``steps``
+    timed ones.  Returns (rows/s, cores, rows per step, mean wall s per timed step, sample
+    description).  ``route="lu"`` (p = 1 only) times the paper's LU inversion instead."""
     import multiprocessing as mp
     import numpy as np
     import oracle
     m = a.row_sizes()
     rng = np.random.default_rng(seed)
     perm = rng.permutation(a.n)
-    # calibrate on a few rows in this process (single thread)
     t0 = time.perf_counter()
     k0 = 0
-    while time.perf_counter() - t0 < 0.5 and k0 < a.n:
+    while time.perf_counter() - t0 < 0.5 and k0 < a.n:            # calibrate (one thread)
         if route == "lu":
             oracle.invroot_lu(a.rowptr, a.colind, a.vals, rows=[int(perm[k0])])
         else:
@@ -143,11 +174,36 @@ def time_oracle(a, p, seconds, seed=3, steps=1, warmup=0, route="eig"):
     sample = (f"{nst} timed step(s) after {warmup} untimed, {k} of {a.n} rows each "
               f"(slices of a seeded permutation, seed {seed}), mean m {msum / done:.1f}, "
               f"{dt:.2f} s wall on {cores} processes")
-    return done / dt, cores, sample
+    return done / dt, cores, k, dt / nst, sample
+
+
+def oracle_values(a, p, rows=None, sign=-1):
+    """The oracle's values for ``rows`` (None: every row) on the host cores (forked pool;
+    called before this process makes any CUDA call).  Returns (values, wall seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    ref = oracle.pool.invroot(a.rowptr, a.colind, a.vals, p, rows=rows, sign=sign,
+                              processes=min(host_cores(), 64), start="fork")
+    return ref, time.perf_counter() - t0
+
+
+def row_errors(a, y, ref, rows=None):
+    """Per-row ||y_j - ref_j|| / ||ref_j|| over ``rows`` (None: all rows)."""
+    import numpy as np
+    rp = a.rowptr.astype(np.int64)
+    if rows is None:
+        d2 = np.add.reduceat((y - ref) ** 2, rp[:-1])
+        r2 = np.add.reduceat(ref ** 2, rp[:-1])
+        return np.sqrt(d2 / r2)
+    out = []
+    for j in rows:
+        s = slice(rp[j], rp[j + 1])
+        out.append(float(np.linalg.norm(y[s] - ref[s]) / np.linalg.norm(ref[s])))
+    return np.array(out)
 
 
 # ----------------------------------------------------------------------------------------
-def make_workload(name, p, n=0, scale=1):
+def make_workload(name, n=0, scale=1):
     """The named workload with n rows (0: its default size), n x scale rows in all."""
     import inspect
     import workloads as wl
@@ -162,6 +218,11 @@ def make_workload(name, p, n=0, scale=1):
     if n <= 0:
         n = inspect.signature(fn).parameters["n"].default
     return fn(n=n * scale)
+
+
+def describe(name, a, p, sign=-1):
+    root = "A^(-1/p)" if sign < 0 else "A^(1/p)"
+    return f"{name}(n={a.n},nnz={a.nnz},p={p}{'' if sign < 0 else ',' + root})"
 
 
 def clocks_start():
@@ -232,30 +293,171 @@ def traffic_for(kernel_src):
     return ent.get("dram_bytes_per_launch")
 
 
+def fp32_alu_peak_tflops(sm_mhz):
+    """FP32 FMA peak of GB300's CUDA cores: 152 SMs x 128 lanes x 2 flops per clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------------------------------
+# GPU timing helpers
+# ----------------------------------------------------------------------------------------
+def timed_forward(sm, plan, vals, out, flush, steps, warmup):
+    """``warmup`` untimed forwards, then ``steps`` timed ones (L2 flushed before each, not
+    timed), CUDA events on the launching stream.  Returns per-step ms and the reports."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        sm.submat_invroot(plan, vals, out)
+    torch.cuda.synchronize()
+    ms, reps = [], []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sm.submat_invroot(plan, vals, out)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        reps.append(plan.report())
+    return ms, reps
+
+
+def roofline_mixed(reps, pk, pk_kind):
+    """Roofline of fwd_mixed_kernel: the method's flops per launch over the kernel's mean
+    CUDA-event time, against the measured dense BF16 (= FP16) sustained rate."""
+    kern_ms = statistics.mean(r["ms_kernel"] for r in reps)
+    alg = statistics.mean(r["flops_alg"] for r in reps)
+    executed = statistics.mean(r["flops_tensor"] for r in reps)
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    achieved = alg / (kern_ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": "fwd_mixed_kernel", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_kind": f"{pk_kind} bf16 dense sustained (FP16 rate = BF16 rate)",
+            "flops_per_launch": alg, "ms_kernel": kern_ms,
+            "work": "sum over rows of k_j (p+1) 2 m_j^3 (executed iterations, true orders)",
+            "executed_tensor_tflops": executed / (kern_ms / 1e3) / 1e12,
+            "executed_tensor_frac": executed / (kern_ms / 1e3) / 1e12 / peak,
+            "executed_work": "15 FP16 slice products x 2 m_j^3 per executed GEMM"}
+
+
+def roofline_fp64(reps):
+    kern_ms = statistics.mean(r["ms_kernel"] for r in reps)
+    alg = statistics.mean(r["flops_alg"] for r in reps)
+    achieved = alg / (kern_ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": "fwd_fp64_kernel", "achieved": achieved,
+            "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal FP64 rate",
+            "flops_per_launch": alg, "ms_kernel": kern_ms, "traffic": None,
+            "work": "sum over rows of k_j (p+1) 2 m_j^3 (executed iterations, true orders)"}
+
+
+def run_extra(sm, spec, a, ref, rows_checked, flush, pk, pk_kind, clocks_mhz):
+    """One extra workload: plan, warm-up, timed forwards (median), accuracy vs the oracle."""
+    import numpy as np
+    import torch
+    name, wname, p, prec, sign, _, warm, steps = spec
+    plan = sm.submat_plan(a.rowptr, a.colind, p, precision=prec, root_sign=sign)
+    vals = torch.tensor(a.vals, device="cuda")
+    out = torch.empty_like(vals)
+    ms, reps = timed_forward(sm, plan, vals, out, flush, steps, warm)
+    med = statistics.median(ms)
+    y = out.cpu().numpy()
+    err = row_errors(a, y, ref, rows_checked)
+    rec = {"workload": describe(wname, a, p, sign), "precision": prec,
+           "value": a.n / (med / 1e3), "unit": UNIT, "ms_per_step_median": med,
+           "steps": steps, "warmup": warm,
+           "max_row_rel_err_vs_oracle": float(err.max()),
+           "rows_checked": "all" if rows_checked is None else int(len(rows_checked)),
+           "tol": 1e-10 if prec == "fp64" else 1e-6,
+           "fallback_rows": int(reps[-1]["n_fallback"]),
+           "iters_mean": reps[-1]["iters_sum"] / max(1, a.n),
+           "roofline": roofline_fp64(reps) if prec == "fp64" else roofline_mixed(reps, pk, pk_kind)}
+    if rows_checked is not None:
+        rec["rows_sample"] = "seeded (seed 3) sample stratified by row size, incl. the " \
+                             "smallest and largest rows"
+    if name == "backward":
+        rec.update(backward_block(sm, plan, a, vals, flush, steps, warm, clocks_mhz))
+    del plan
+    return rec
+
+
+def backward_block(sm, plan, a, vals, flush, steps, warm, clocks_mhz):
+    """The adjoint on the differentiation workload: L = sum(W * Y), W ~ N(0,1) on the
+    pattern (seed 1); timed backward calls (median) and the gradient against the oracle's
+    over every stored entry (computed before the GPU work)."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    w = torch.tensor(wl.random_on_pattern(a, seed=1), device="cuda")
+    stream = torch.cuda.current_stream()
+    sm.submat_invroot(plan, vals)
+    for _ in range(warm):
+        sm.submat_invroot_backward(plan, w)
+    torch.cuda.synchronize()
+    ms = []
+    g = None
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g = sm.submat_invroot_backward(plan, w)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    med = statistics.median(ms)
+    gref = _PRE["grad_ref"]
+    gh = g.cpu().numpy()
+    m = a.row_sizes().astype(np.float64)
+    work = float((16.0 * m ** 3).sum())
+    mhz = clocks_mhz or 2070.0
+    peak = fp32_alu_peak_tflops(mhz)
+    achieved = work / (med / 1e3) / 1e12
+    return {"backward": {
+        "ms_per_call_median": med, "value": a.n / (med / 1e3), "unit": UNIT,
+        "grad_rel_err_vs_oracle": float(np.linalg.norm(gh - gref) / np.linalg.norm(gref)),
+        "grad_max_abs_err_rel_to_max": float(np.abs(gh - gref).max() / np.abs(gref).max()),
+        "tol": 1e-10,
+        "roofline": {"bound": "alu", "kernel": "backward_kernel", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_kind": f"FP32 FMA rate at {mhz:.0f} MHz (152 SMs x 128 lanes x 2)",
+                     "work": "16 m_j^3 per row (Jacobi sweeps and eigenvector products "
+                             "counted as FP64-equivalent flops, executed in double-float "
+                             "FP32 arithmetic)"}}}
+
+
+_PRE = {}
+
+
+# ----------------------------------------------------------------------------------------
 def main():
     args = parse()
     rank, world, local = dist_env()
     import numpy as np
 
     log(f"generating {args.workload}")
-    a = make_workload(args.workload, args.p, args.n, scale=world)
+    a = make_workload(args.workload, args.n, scale=world)
     p = args.p
     log(f"n={a.n} nnz={a.nnz}")
-    workload_name = f"{args.workload}(n={a.n},nnz={a.nnz},p={p})"
+    workload_name = describe(args.workload, a, p)
 
     if args.impl == "reference":
         if rank != 0:
             return
-        v, cores, sample = time_oracle(a, p, args.oracle_seconds, steps=args.steps,
-                                       warmup=args.warmup)
+        v, cores, k, wall, sample = time_oracle_sampled(a, p, args.oracle_seconds,
+                                                        steps=args.steps, warmup=args.warmup)
         extra = {}
         if p == 1:          # the paper's own p = 1 route (LU inversion), reported beside it
-            vl, cl, sl = time_oracle(a, p, args.oracle_seconds, steps=args.steps,
-                                     warmup=args.warmup, route="lu")
+            vl, cl, _, _, sl = time_oracle_sampled(a, p, args.oracle_seconds, steps=args.steps,
+                                                   warmup=args.warmup, route="lu")
             extra["paper_lu_p1"] = {"value": vl, "unit": UNIT, "cores": cl, "sample": sl}
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * a.n / v,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall,
+            "step_rows": k, "ms_full_workload_extrapolated": 1e3 * a.n / v,
+            "step_note": (f"a step is a sample of {k} of the workload's {a.n} rows; "
+                          "ms_full_workload_extrapolated scales the sampled rate to all rows"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -265,6 +467,48 @@ def main():
         }))
         return
 
+    # ---- host phase: the oracle on the host cores, before any CUDA call ------------------
+    do_extras = (rank == 0 and world == 1 and not args.no_extras)
+    extras = []
+    if do_extras:
+        want = set(x for x in args.extras.split(",") if x) or None
+        extras = [e for e in EXTRAS if want is None or e[0] in want]
+    cpu_base, ref_all = None, None
+    if rank == 0 and world == 1:
+        log("oracle on every row (CPU baseline)")
+        ref_all, dt = oracle_values(a, p)
+        cores = min(host_cores(), 64)
+        cpu_base = {"value": a.n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                    "sample": f"the whole workload: all {a.n} rows, one pass, {dt:.2f} s wall "
+                              f"on {cores} single-threaded processes"}
+        log(f"oracle: {a.n / dt:.1f} rows/s on {cores} cores")
+    extra_inputs = {}
+    import workloads as wl
+    for spec in extras:
+        name, wname, ep, prec, sign, nrows, _, _ = spec
+        key = (wname, args.n if wname == args.workload else 0)
+        if wname == args.workload:
+            ea = a
+        elif key in _PRE:
+            ea = _PRE[key]
+        else:
+            log(f"generating {wname}")
+            ea = make_workload(wname, 0)
+            _PRE[key] = ea
+        rows = None if nrows == 0 else wl.stratified_rows(ea.row_sizes(), nrows, seed=3)
+        log(f"oracle for {name}: {'all' if rows is None else len(rows)} rows")
+        if ea is a and ep == p and sign == -1 and rows is None:
+            ref = ref_all
+        else:
+            ref, _ = oracle_values(ea, ep, rows=rows, sign=sign)
+        if name == "backward":
+            import oracle
+            w = wl.random_on_pattern(ea, seed=1)
+            log("oracle gradient (every row)")
+            _PRE["grad_ref"] = oracle.pool.grad(ea.rowptr, ea.colind, ea.vals, ep, w,
+                                                processes=min(host_cores(), 64), start="fork")
+        extra_inputs[name] = (ea, ref, rows)
+
     import torch
     import paper_1710_10899_gb300 as sm
     torch.cuda.set_device(local)
@@ -272,15 +516,6 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-
-    # rows of this rank: a contiguous, cost-balanced shard of the world-times-larger matrix
-    # (weak scaling: about the 1-GPU workload's rows per rank; with world == 1 all rows)
-    cpu_base = None
-    if rank == 0 and world == 1:
-        # time the oracle before any GPU work starts the CUDA context in the pool's parent
-        log("timing the oracle on the host cores")
-        cpu_base = time_oracle(a, p, args.oracle_seconds)
-        log(f"oracle: {cpu_base[0]:.1f} rows/s on {cpu_base[1]} cores")
 
     log("plan")
     plan = sm.submat_plan(a.rowptr, a.colind, p, precision=args.precision, shard=(rank, world))
@@ -296,7 +531,7 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region: K steps, L2 flushed before each (flush not timed) --------------
-    ms_steps, ms_kern, flops_t, flops_64, fallbacks = [], [], 0.0, 0.0, 0
+    ms_steps, reps = [], []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -310,11 +545,7 @@ def main():
         e1.record(stream)
         e1.synchronize()
         ms_steps.append(e0.elapsed_time(e1))
-        rep = plan.report()
-        ms_kern.append(rep["ms_kernel"])
-        flops_t += rep["flops_tensor"]
-        flops_64 += rep["flops_fp64"]
-        fallbacks += rep["n_fallback"]
+        reps.append(plan.report())
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -327,21 +558,23 @@ def main():
     ms_per_step = total_ms / args.steps
     rows_total = a.n                               # all shards together
     value = rows_total / (ms_per_step / 1e3)
-
     log(f"timed: {ms_per_step:.2f} ms/step")
-    # ---- accuracy on sampled rows (outside the timed region) ----------------------------
+
+    # ---- accuracy (outside the timed region) ---------------------------------------------
     y = out.cpu().numpy()
-    max_err = None
-    if rank == 0:
+    acc = {}
+    if rank == 0 and ref_all is not None:
+        err = row_errors(a, y, ref_all)
+        acc = {"max_row_rel_err_vs_oracle": float(err.max()),
+               "rows_checked_vs_oracle": int(a.n),
+               "rows_over_tol": int((err > (1e-6 if args.precision == "mixed" else 1e-10)).sum())}
+    elif rank == 0:
         import oracle
         rng = np.random.default_rng(11)
         rows = row_b + rng.choice(row_e - row_b, size=min(48, row_e - row_b), replace=False)
-        errs = []
-        for j in rows:
-            s = slice(a.rowptr[j], a.rowptr[j + 1])
-            ref = oracle.row_segment(a.rowptr, a.colind, a.vals, p, int(j))
-            errs.append(float(np.linalg.norm(y[s] - ref) / np.linalg.norm(ref)))
-        max_err = max(errs)
+        ref = oracle.invroot(a.rowptr, a.colind, a.vals, p, rows=[int(j) for j in rows])
+        acc = {"max_row_rel_err_vs_oracle": float(row_errors(a, y, ref, rows).max()),
+               "rows_checked_vs_oracle": int(len(rows))}
 
     # ---- end to end through the C ABI with host buffers (pinned) ------------------------
     hin = torch.tensor(a.vals).pin_memory()
@@ -360,78 +593,77 @@ def main():
         t = torch.tensor([e2e_step], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_step = float(t.item())
-
     log(f"e2e: {e2e_step:.2f} ms/step")
-    # ---- the all-FP64 GPU path on the same input (one step, for the comparison) ----------
+
+    # ---- the all-FP64 GPU path on the same input ------------------------------------------
     fp64 = None
     if world == 1 and not args.no_fp64_compare and args.precision == "mixed":
-        log("FP64 path (one step)")
+        log(f"FP64 path (1 warm-up, median of {args.fp64_steps})")
         pl64 = sm.submat_plan(a.rowptr, a.colind, p, precision="fp64")
         o64 = torch.empty_like(vals)
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sm.submat_invroot(pl64, vals, o64)
-        e1.record(stream)
-        e1.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        log(f"FP64 path: {ms64:.1f} ms")
-        r64 = pl64.report()
-        d = (out - o64).cpu().numpy()
+        ms64, reps64 = timed_forward(sm, pl64, vals, o64, flush, max(1, args.fp64_steps), 1)
+        med64 = statistics.median(ms64)
+        log(f"FP64 path: {med64:.1f} ms")
         y64 = o64.cpu().numpy()
-        worst = 0.0
-        for j in range(0, a.n, max(1, a.n // 4096)):
-            s = slice(a.rowptr[j], a.rowptr[j + 1])
-            worst = max(worst, float(np.linalg.norm(d[s]) / np.linalg.norm(y64[s])))
-        fp64 = {"value": a.n / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
-                "tflops_fp64": r64["flops_fp64"] / (ms64 / 1e3) / 1e12,
-                "mixed_vs_fp64_max_row_rel_err": worst,
-                "speedup_mixed_over_fp64": ms64 / ms_per_step}
+        fp64 = {"value": a.n / (med64 / 1e3), "unit": UNIT, "ms_per_step_median": med64,
+                "steps": len(ms64), "warmup": 1, "ms_per_step_all": ms64,
+                "roofline": roofline_fp64(reps64),
+                "mixed_vs_fp64_max_row_rel_err": float(row_errors(a, y, y64).max()),
+                "speedup_mixed_over_fp64": med64 / statistics.median(ms_steps)}
+        if ref_all is not None:
+            fp64["max_row_rel_err_vs_oracle"] = float(row_errors(a, y64, ref_all).max())
+            fp64["rows_checked_vs_oracle"] = int(a.n)
         del pl64
 
-    if world > 1:                                   # the job's tensor flops (all shards)
-        t = torch.tensor([flops_t], device=dev, dtype=torch.float64)
+    reps_all = reps
+    if world > 1:                                   # the job's flops (all shards)
+        t = torch.tensor([sum(r["flops_alg"] for r in reps)], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         flops_job = float(t.item())
     else:
-        flops_job = flops_t
+        flops_job = sum(r["flops_alg"] for r in reps_all)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
     pk, pk_kind = peaks()
-    kern_ms = statistics.mean(ms_kern)
-    flops_per_launch = flops_t / args.steps
     if args.precision == "mixed":
-        achieved = flops_per_launch / (kern_ms / 1e3) / 1e12
-        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-        roof = {"bound": "tensor", "kernel": "fwd_mixed_kernel", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_kind": f"{pk_kind} bf16 dense sustained (FP16 rate = BF16 rate)",
-                "traffic": traffic_for("paper_1710_10899_gb300/csrc/fwd_mixed.cu")}
+        roof = roofline_mixed(reps, pk, pk_kind)
+        roof["traffic"] = traffic_for("paper_1710_10899_gb300/csrc/fwd_mixed.cu")
     else:
-        achieved = (flops_64 / args.steps) / (kern_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": "fwd_fp64_kernel", "achieved": achieved,
-                "peak": 1.25, "unit": "TFLOP/s", "frac": achieved / 1.25,
-                "peak_kind": "nominal FP64 rate", "traffic": None}
+        roof = roofline_fp64(reps)
+
+    # ---- extra workloads (1 GPU only; outside the main timed region) ----------------------
+    extra_out = {}
+    if extras:
+        del plan
+        torch.cuda.empty_cache()
+        mhz = clocks["sm_mhz"] if clocks else None
+        for spec in extras:
+            name = spec[0]
+            ea, ref, rows = extra_inputs[name]
+            log(f"extra: {name}")
+            try:
+                extra_out[name] = run_extra(sm, spec, ea, ref, rows, flush, pk, pk_kind, mhz)
+            except Exception as e:                  # report, keep the main line
+                extra_out[name] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f16-pair/f32acc+f64" if args.precision == "mixed" else "f64",
+        "dtype": DTYPE_MIXED if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": workload_name, "precision": args.precision,
                    "l2": "flushed before every step (512 MB write, untimed)",
                    "parallelism": (f"rows sharded over {world} GPUs (cost-balanced contiguous "
                                    f"ranges, whole matrix on every GPU)") if world > 1 else "1 GPU"},
-        "tflops": (flops_job / args.steps / (ms_per_step / 1e3)) / 1e12,
-        # the same products counted once each (2 m^3 per GEMM instead of 15 slice products)
-        "gemm_tflops": (flops_job / (15.0 if args.precision == "mixed" else 1.0)
-                        / args.steps / (ms_per_step / 1e3)) / 1e12,
-        "max_row_rel_err_vs_oracle_sampled": max_err,
-        "fallback_rows_per_step": fallbacks / args.steps,
+        "tflops_alg": (flops_job / args.steps / (ms_per_step / 1e3)) / 1e12,
+        **acc,
+        "fallback_rows_per_step": statistics.mean(r["n_fallback"] for r in reps),
+        "iters_mean": reps[-1]["iters_sum"] / max(1, reps[-1]["n_rows"]),
         "roofline": roof,
         "e2e": {"value": rows_total / (e2e_step / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(a.nnz * 8 * world),
@@ -442,9 +674,9 @@ def main():
     if fp64 is not None:
         line["fp64_path"] = fp64
     if cpu_base is not None:
-        v, cores, sample = cpu_base
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": sample}
+        line["cpu_baseline"] = cpu_base
+    if extra_out:
+        line["extras"] = extra_out
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
