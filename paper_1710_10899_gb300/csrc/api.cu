@@ -15,7 +15,7 @@
 
 namespace submat {
 cudaError_t set_attr_mixed();
-int mixed_ctas_per_sm();           // CTAs per SM of the tcgen05 engine
+int mixed_ctas_per_sm(int engine); // CTAs per SM of a mixed-path engine
 cudaError_t set_attr_fp64();
 cudaError_t set_attr_eig();
 }  // namespace submat
@@ -193,6 +193,7 @@ submat_status enqueue_forward(submat_plan_t P, const double* in, double* out, cu
   a.sign = P->opts.root_sign;
   a.ld = P->ld;
   a.engine = P->opts.precision == SUBMAT_PREC_MIXED_F16_SYNC ? 1 : 0;
+  a.queue = &P->d_ctr->queue;
   a.tm_a = P->tm_a;
   a.tm_b = P->tm_b;
   a.stall = P->d_stall;
@@ -432,7 +433,7 @@ static submat_status plan_impl(const submat_csr* csr, int32_t p, const submat_op
   size_t stride = mixed ? scratch_mixed(P->ld) : std::max(scratch_eig(mp), scratch_fp64(mp));
   stride = (stride + 1023) / 1024 * 1024;
   P->stride = stride;
-  const int ctas = (o.precision == SUBMAT_PREC_MIXED_F16) ? mixed_ctas_per_sm() : 1;
+  const int ctas = (o.precision == SUBMAT_PREC_MIXED_F16) ? mixed_ctas_per_sm(0) : 1;
   P->grid = std::max(1, std::min(P->n_sm * ctas, P->n_jobs));
   PLAN_TRY(cudaMalloc(&P->d_scratch, stride * (size_t)P->grid));
   if (mixed && o.precision == SUBMAT_PREC_MIXED_F16) {

@@ -40,7 +40,8 @@ struct FwdArgs {
   CUtensorMap tm_a;          // mixed tcgen05 engine: A tiles (16 x 128) of the scratch planes
   CUtensorMap tm_b;          //                       B tiles (16 x 96)
   int32_t ld;                // mixed path: leading dimension of the scratch planes
-  int32_t engine;            // mixed path: 0 = tcgen05, 1 = mma.sync
+  int32_t engine;            // mixed path: 0 = tcgen05, 1 = mma.sync, 2 = small (shared memory)
+  int32_t* queue;            // mixed path: work-queue head of this launch (its rows: order[0, n))
   const int32_t* rowptr;
   const int32_t* colind;
   const int32_t* m;          // [n] row sizes

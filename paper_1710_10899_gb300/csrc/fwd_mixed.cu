@@ -23,10 +23,11 @@
 // constants; X's exponent is predicted from its last measured maximum).  A product is the sum over levels L = s + t <= 4 of
 // 2^(-8L) sum_{s+t=L} Q_s^A Q_t^B (15 FP16 MMAs per k-step, FP32 accumulation per level).
 // The products of these integers are exact, and every level-0 partial sum is an integer
-// below 2^14 K, so for K <= 1024 the tensor cores accumulate level 0 exactly (level 1
-// multiplies q0 by a residual slice of either sign: its sums stay far below 2^24 in practice,
-// and its weight is 2^-8); levels 2..4 carry weights 2^-16..2^-32.  Orders above 1024 raise
-// every exponent by one (exp_bias), which keeps level 0 exact up to K = 4096.  The levels dropped (s + t >= 5) bound the normwise error of a
+// below 2^14 K (plus 2^16 from the affine term below), so for K <= 1008 the tensor cores
+// accumulate level 0 exactly (level 1 multiplies q0 by a residual slice of either sign: its
+// sums stay far below 2^24 in practice, and its weight is 2^-8); levels 2..4 carry weights
+// 2^-16..2^-32.  Orders above 1008 raise every exponent by one (exp_bias), which keeps level 0
+// exact up to K = 4092.  The levels dropped (s + t >= 5) bound the normwise error of a
 // product near 2^-39 sqrt(K) of max|A| max|B|.  The epilogue combines the levels in
 // double-float (FP32 pairs) and re-splits the result.  (With four planes, the ~2^-31
 // per-product error, kept by every iteration, left ~6e-7 in the result; measured.)
@@ -34,10 +35,14 @@
 // GEMM engines (template parameter TC):
 //   TC = true  (default): tcgen05.mma kind::f16, M = 128, N = 96, the five level
 //              accumulators in one 480-column TMEM buffer, drained in phases (levels
-//              combined into shared memory and TMEM released; the affine step and the
+//              combined into shared memory and TMEM released; scaling, slicing and the
 //              stores; the mirror images) so the next tile's MMAs overlap the later
 //              phases; operands moved by TMA (SWIZZLE_32B, 16-wide k-slices) through a
-//              3-stage mbarrier pipeline.  Roles: warps 0-7 run the epilogue (two per TMEM
+//              3-stage mbarrier pipeline.  A full-width tile issues the fifteen plane
+//              products of a k-step as eight MMAs over B's concatenated planes (N up to
+//              240), and the affine term alpha Y (Y = B) enters the accumulators through
+//              MMAs with an exact identity operand -alpha' I on the k-steps of the tile's
+//              diagonal block, so the epilogue reads no Y.  Roles: warps 0-7 run the epilogue (two per TMEM
 //              lane quarter), warp 8 issues TMA, warp 9 issues MMAs, warps 10-11 apply the
 //              iteration's step to the carried column (384 threads).
 //              All working matrices are symmetric, so a row-major B read as K-major
@@ -68,9 +73,10 @@ constexpr int E_M = 0;             // |M| <= 1 (eigenvalues of M_k lie in (0, 1]
 constexpr int kPlanesPerCta = 35;  // 6 matrices x 5 planes, 4 planes of room for S_j (FP64),
                                    // 1 plane for the tracked vectors
 
-// Every product of the iteration has the form C = c (alpha Y - A Y'), i.e. the step matrix
-// T = c (alpha I - A) applied to Y (Y' = Y, or Y = A for the X update of p = 1): the
-// epilogue reads Y's entry at the output position (all matrices are symmetric).  Flags:
+// Every product of the iteration has the form C = c (alpha Y - A Y), i.e. the step matrix
+// T = c (alpha I - A) applied to Y, with A = M_k and Y the B operand (all matrices are
+// symmetric polynomials in S, so they commute).  The tcgen05 engine adds -alpha Y to the
+// accumulators with MMAs; the mma.sync engine reads Y's entry at the output position.  Flags:
 // accumulate ||C - I||_F^2 over the leading m x m block, and/or max |C|.
 enum EpiFlag { EPI_NORM = 1, EPI_AMAX = 2 };
 
@@ -91,11 +97,11 @@ struct GemmIO {     // what every GEMM call shares within one submatrix
 // Exponent for values bounded by b (with a relative margin for rounding).
 __device__ __forceinline__ int exp_of(float b) { return exp_bound(b * (1.f + 1e-6f)); }
 
-// Extra exponent for orders above 1024: with |q0| <= 64 every level-0 partial sum stays an
-// integer below 2^12 K < 2^24 up to K = 4096 (one of the ~39 bits is given up).  Level 0
+// Extra exponent for orders above 1008: with |q0| <= 64 every level-0 partial sum stays an
+// integer below 2^12 K + 2^14 < 2^24 up to K = 4092 (one of the ~39 bits is given up).  Level 0
 // matters most: for same-sign data (overlap matrices) its sums grow linearly with K, while
 // level 1 multiplies q0 by a rounding residual of either sign and grows like sqrt(K).
-__device__ __forceinline__ int exp_bias(int mp) { return mp > 1024 ? 1 : 0; }
+__device__ __forceinline__ int exp_bias(int mp) { return mp > 1008 ? 1 : 0; }
 
 // Slices of 8 consecutive values -> one 16-byte store per plane.
 __device__ __forceinline__ void store8_slices(__half* q, size_t plane, size_t idx0,
@@ -462,6 +468,12 @@ constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 107520 B
 constexpr int TC_CH = TC_N / 8;                        // 8-column chunks per tile row (12)
 constexpr int TC_SROW = 4 * TC_CH + 1;                 // units per staged row (49)
 constexpr int TC_STAGING_BYTES = TC_M * TC_SROW * 16;  // 100352 B
+// Identity operand of the affine term (see gemm_tc): a K-major 240 x 16 FP16 tile whose only
+// nonzeros, -alpha', sit at (112 + k, k); rows [112 - o, 240 - o) of it are the 128 x 16
+// slice of -alpha' I for a k-step o = 16 kt - 128 tm columns into the tile's diagonal block.
+constexpr int TC_Z_ROWS = TC_M + TC_M - TC_K;          // 240
+constexpr int TC_Z_BYTES = TC_Z_ROWS * TC_K * 2;       // 7680 B (1024-aligned in the layout)
+constexpr float kAlphaQuantum = 1.f / 64.f;            // alpha' = alpha 2^(7 - e) is an integer
 constexpr int TC_BUF_COLS = NSL * TC_N;                // 480 TMEM columns
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;           // polls before a wait gives up
 constexpr uint32_t TC_TMEM_COLS = 512;
@@ -486,6 +498,7 @@ struct TcState {            // pipeline counters; each role keeps its own copy
 struct TcCtx {
   unsigned char* stages;    // 1024-aligned shared memory
   uint4* staging;           // [TC_M][TC_SROW] units of the tile being drained
+  __half* z;                // identity operand (TC_Z_BYTES, 1024-aligned)
   uint64_t* full;           // [TC_STAGES]
   uint64_t* empty;          // [TC_STAGES]
   uint64_t* tmem_full;      // accumulators ready
@@ -545,6 +558,64 @@ __device__ __forceinline__ void store8_planes(__half* q, size_t plane, int ld, i
   }
 }
 
+// Half index of element (row q, column k) of a K-major 16-wide tile in the 32-byte swizzle
+// that TMA writes and the MMA reads: 32-byte rows, the two 16-byte halves of row q swapped
+// when bit 2 of q is set (address bit 4 ^= address bit 7; the tile is 256-byte aligned).
+__device__ __forceinline__ int sw32_index(int q, int k) {
+  return q * TC_K + (((k >> 3) ^ ((q >> 2) & 1)) << 3) + (k & 7);
+}
+
+// The MMAs of one k-step.  A full-width tile (N = 96) concatenates B's planes: the five B
+// planes of a stage lie back to back (96 rows each), and level L = s + t of A_s B_t sits at
+// TMEM columns 96 L, so A_s times B planes t0..t1 is one MMA with N = 96 (t1 - t0 + 1) whose
+// output columns start at 96 (s + t0).  The fifteen plane products become eight MMAs (N = 240,
+// 240, 192, 192, 144, 144, 192, 96), each reading its A plane once.  A narrower last tile
+// issues the fifteen products separately with N = nw.
+__device__ __forceinline__ void mma_kstep_full(uint32_t d0, uint64_t da0, uint64_t db0,
+                                               uint32_t acc0) {
+  constexpr uint32_t i240 = tc::idesc_f16(TC_M, 240), i192 = tc::idesc_f16(TC_M, 192),
+                     i144 = tc::idesc_f16(TC_M, 144), i96 = tc::idesc_f16(TC_M, 96);
+  constexpr uint64_t PA = TC_A_PLANE >> 4, RB = (TC_K * 2) >> 4;   // 16-byte units
+  // s = 0: B rows 0..479 -> columns 0..479 (overwrite at the first k-step)
+  tc::mma_f16(d0 + 0, da0, db0 + 0 * RB, i240, acc0);
+  tc::mma_f16(d0 + 240, da0, db0 + 240 * RB, i240, acc0);
+  // s = 1: B rows 0..383 -> columns 96..479
+  tc::mma_f16(d0 + 96, da0 + PA, db0 + 0 * RB, i192, 1u);
+  tc::mma_f16(d0 + 288, da0 + PA, db0 + 192 * RB, i192, 1u);
+  // s = 2: B rows 0..287 -> columns 192..479
+  tc::mma_f16(d0 + 192, da0 + 2 * PA, db0 + 0 * RB, i144, 1u);
+  tc::mma_f16(d0 + 336, da0 + 2 * PA, db0 + 144 * RB, i144, 1u);
+  // s = 3: B rows 0..191 -> columns 288..479; s = 4: B rows 0..95 -> columns 384..479
+  tc::mma_f16(d0 + 288, da0 + 3 * PA, db0, i192, 1u);
+  tc::mma_f16(d0 + 384, da0 + 4 * PA, db0, i96, 1u);
+}
+__device__ __forceinline__ void mma_kstep_narrow(uint32_t d0, uint64_t da0, uint64_t db0,
+                                                 uint32_t idesc, uint32_t acc0) {
+#pragma unroll
+  for (int L = 0; L < NSL; ++L) {
+#pragma unroll
+    for (int sa_i = 0; sa_i <= L; ++sa_i) {
+      const uint64_t da = da0 + (uint64_t)((sa_i * TC_A_PLANE) >> 4);
+      const uint64_t db = db0 + (uint64_t)(((L - sa_i) * TC_B_PLANE) >> 4);
+      tc::mma_f16(d0 + L * TC_N, da, db, idesc, sa_i != 0 ? 1u : acc0);
+    }
+  }
+}
+// The affine term: -alpha' I (one exact FP16 plane, level 0) times B's five planes, added to
+// levels 0..4.  Full tiles: two MMAs with N = 240 over the concatenated planes.
+__device__ __forceinline__ void mma_identity_full(uint32_t d0, uint64_t dz, uint64_t db0) {
+  constexpr uint32_t i240 = tc::idesc_f16(TC_M, 240);
+  constexpr uint64_t RB = (TC_K * 2) >> 4;
+  tc::mma_f16(d0 + 0, dz, db0, i240, 1u);
+  tc::mma_f16(d0 + 240, dz, db0 + 240 * RB, i240, 1u);
+}
+__device__ __forceinline__ void mma_identity_narrow(uint32_t d0, uint64_t dz, uint64_t db0,
+                                                    uint32_t idesc) {
+#pragma unroll
+  for (int t = 0; t < NSL; ++t)
+    tc::mma_f16(d0 + t * TC_N, dz, db0 + (uint64_t)((t * TC_B_PLANE) >> 4), idesc, 1u);
+}
+
 // C = A B^T on the tcgen05 engine (see the header comment).  All TC_THREADS threads call it.
 // The GEMMs of one iteration run back to back with the GEMM warps' barrier between them;
 // full_in / full_out make the first one start and the last one end with a whole-block
@@ -600,11 +671,20 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
     }
   } else if (warp == TC_MMA_WARP) {
     if (lane == 0) {                                   // ---- MMA issuer
+      // -alpha' on the identity operand's band (the previous GEMM's MMAs have completed:
+      // its epilogue drained every tile before the barrier that started this GEMM)
+      const __half nz = __float2half_rn(-ldexpf(io.alpha, 7 - A.e));
+      for (int k = 0; k < TC_K; ++k) c.z[sw32_index(TC_M - TC_K + k, k)] = nz;
+      tc::fence_proxy_async_shared();
+      const uint64_t dz0 = tc::desc_sw32(tc::saddr(c.z));
       for (int t = 0; t < ntiles && !*c.abort_s; ++t) {
         int tm, tn;
         tc_tile(t, ntn, tm, tn);
         const int nw = min(TC_N, mp - tn * TC_N);      // 96, or 16..80 for the last tile
+        const bool full = nw == TC_N;
         const uint32_t idesc = tc::idesc_f16(TC_M, nw);
+        // k-steps inside the tile's diagonal block carry the affine term
+        const int kd0 = tm * (TC_M / TC_K), kd1 = min(KT, kd0 + TC_M / TC_K);
         // the single accumulator buffer is free once the epilogue has read the previous tile
         if (st.tmt >= 1 && !tc::mbar_wait(c.tmem_empty, (st.tmt - 1) & 1, TC_WAIT_LIMIT)) {
           *c.abort_s = 1;
@@ -620,21 +700,23 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
             break;
           }
           tc::tc_fence_after();
-          // operand descriptors of the stage; every plane offset below is a compile-time
+          // operand descriptors of the stage; every offset added below is a compile-time
           // constant added to the 14-bit start-address field (no carry: shared addresses
           // stay below 2^18 bytes)
           const uint32_t sa = tc::saddr(c.stages + s * TC_STAGE_BYTES);
           const uint64_t da0 = tc::desc_sw32(sa);
           const uint64_t db0 = tc::desc_sw32(sa + NSL * TC_A_PLANE);
           const uint32_t acc0 = kt != 0;               // the first k-step overwrites
-#pragma unroll
-          for (int L = 0; L < NSL; ++L) {
-#pragma unroll
-            for (int sa_i = 0; sa_i <= L; ++sa_i) {
-              const uint64_t da = da0 + (uint64_t)((sa_i * TC_A_PLANE) >> 4);
-              const uint64_t db = db0 + (uint64_t)(((L - sa_i) * TC_B_PLANE) >> 4);
-              tc::mma_f16(d0 + L * TC_N, da, db, idesc, sa_i != 0 ? 1u : acc0);
-            }
+          if (full)
+            mma_kstep_full(d0, da0, db0, acc0);
+          else
+            mma_kstep_narrow(d0, da0, db0, idesc, acc0);
+          if (kt >= kd0 && kt < kd1) {
+            const uint64_t dz = dz0 + (uint64_t)(((TC_M - TC_K) - (kt - kd0) * TC_K) * TC_K * 2 >> 4);
+            if (full)
+              mma_identity_full(d0, dz, db0);
+            else
+              mma_identity_narrow(d0, dz, db0, idesc);
           }
           tc::mma_commit(&c.empty[s]);                 // frees the stage when these MMAs finish
           ++st.cit;
@@ -650,10 +732,9 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
   } else {                                             // ---- epilogue (TMEM lanes 0..127)
     const int q4 = warp & 3, half = warp >> 2;
     const int etid = tid;                              // 0 .. 255 (warps 0..7)
-    // the level sums count in units of cscale = 2^(A.e + B.e - 14), Y's planes in units of
-    // 2^(Y.e - 15)
-    const float alpha_s = ldexpf(io.alpha, Y.e - 15 - (A.e + B.e - 14));
-    const float c_s = ldexpf(io.c, A.e + B.e - 14);
+    // the level sums count in units of cscale = 2^(A.e + B.e - 14) and already hold
+    // A B - alpha Y (the identity operand's MMAs), so C = -c cscale w
+    const float c_s = -ldexpf(io.c, A.e + B.e - 14);
     float nrm = 0.f, amax = 0.f;
     const int rt = q4 * 32 + lane;                    // phase 1: this thread's tile row
     for (int t = 0; t < ntiles; ++t) {
@@ -714,12 +795,7 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
         const int row = tm * TC_M + r;
         if (row >= mp || ch >= nch) continue;
         const int j0 = tn * TC_N + ch * 8;
-        const size_t idx0 = (size_t)row * io.ld + j0;
         uint4* su = c.staging + r * TC_SROW + ch;
-        uint4 yr[NSL];
-#pragma unroll
-        for (int k = 0; k < NSL; ++k)
-          yr[k] = *reinterpret_cast<const uint4*>(Y.q + k * io.plane + idx0);
         float wv[16];
 #pragma unroll
         for (int k2 = 0; k2 < 4; ++k2) {
@@ -732,23 +808,10 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
         float oh[8], ol[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          float yq[NSL];
-#pragma unroll
-          for (int s2 = 0; s2 < NSL; ++s2)
-            yq[s2] = __half2float(reinterpret_cast<const __half*>(&yr[s2])[k]);
-          // y / 2^(Y.e-15) = ya + yb, exact (ya an integer below 2^16, yb below 1)
-          const float ya = __fmaf_rn(yq[0], 256.f, yq[1]);
-          const float yb = __fmaf_rn(yq[2], 1.f / 256.f, __fmaf_rn(yq[3], 1.f / 65536.f,
-                                                                   yq[4] * (1.f / 16777216.f)));
+          // out = -c cscale (wh + wl), as a double-float
           const float wh = wv[2 * k], wl = wv[2 * k + 1];
-          // out = c cscale (alpha' y - w), alpha' = alpha 2^(Y.e-15) / cscale (exact)
-          const float p1 = __fmul_rn(alpha_s, ya);
-          const float e1 = __fmaf_rn(alpha_s, yb, __fmaf_rn(alpha_s, ya, -p1));
-          float d, de;
-          two_sum(p1, -wh, d, de);
-          de = __fadd_rn(de, __fsub_rn(e1, wl));
-          oh[k] = __fmul_rn(c_s, d);
-          ol[k] = __fmaf_rn(c_s, de, __fmaf_rn(c_s, d, -oh[k]));
+          oh[k] = __fmul_rn(c_s, wh);
+          ol[k] = __fmaf_rn(c_s, wl, __fmaf_rn(c_s, wh, -oh[k]));
         }
         store8_planes(C.q, io.plane, io.ld, row, j0, oh, ol, C.e, su, tile_mirror);
         if (flags & EPI_AMAX) {
@@ -994,31 +1057,124 @@ __device__ void gemm_sync(Mat A, Mat B, Mat C, Mat Y, int flags, const GemmIO& i
 }
 
 // ======================================================================================
+// small-submatrix engine: the whole working set in shared memory, warp-level mma.sync
+// ======================================================================================
+// Orders up to kSmallMaxM: every sliced matrix lives in shared memory (leading dimension
+// kSmallLD; 80-byte rows make the eight row addresses of an ldmatrix fall in distinct banks),
+// the gathered S_j in the CTA's global scratch.  A product of padded order mp (16 or 32) is
+// (mp/16) x (mp/8) warp tiles of 16 x 8, one per warp, each running the fifteen plane products
+// of every 16-wide k-step with mma.sync m16n8k16 into five per-level FP32 accumulators (the
+// same exact level arithmetic as the other engines), then C = c (alpha Y - A B) from Y's
+// shared-memory planes.  Two CTAs of 256 threads share an SM.
+constexpr int kSmallMaxM = 32;
+constexpr int kSmallLD = 40;
+constexpr int kSmallPlanes = 26;           // X[2], three M / partial-product buffers, vectors
+constexpr int kSmallVecPlane = 25;
+constexpr int kSmallVmax = 64;             // length of the shared vectors y_s, v_s, w_s, R_s
+constexpr int kSmallCtasPerSm = 2;
+
+__device__ __forceinline__ void ldsm_x2_t(uint32_t* r, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(smem_u32(p)));
+}
+
+__device__ void gemm_small(Mat A, Mat B, Mat C, Mat Y, int flags, const GemmIO& io) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mp = io.mp;
+  const int ntn = mp / 8, ntiles = (mp / 16) * ntn;
+  const size_t plane = io.plane;
+  const float cscale = ldexpf(1.f, A.e + B.e - 14);
+  float nrm = 0.f, amax = 0.f;
+  for (int t = warp; t < ntiles; t += kWarps) {
+    const int i0 = (t / ntn) * 16, j0 = (t % ntn) * 8;
+    float acc[NSL][4];
+#pragma unroll
+    for (int l = 0; l < NSL; ++l)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[l][c] = 0.f;
+    for (int k0 = 0; k0 < mp; k0 += 16) {
+      uint32_t af[NSL][4], bf[NSL][2];
+#pragma unroll
+      for (int l = 0; l < NSL; ++l) {
+        ldsm_x4(af[l], A.q + l * plane + (size_t)(i0 + (lane & 15)) * kSmallLD + k0 + (lane >> 4) * 8);
+        ldsm_x2_t(bf[l], B.q + l * plane + (size_t)(k0 + (lane & 15)) * kSmallLD + j0);
+      }
+#pragma unroll
+      for (int L = 0; L < NSL; ++L)
+#pragma unroll
+        for (int sa = 0; sa <= L; ++sa) mma16816(acc[L], af[sa], bf[L - sa]);
+    }
+    const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci) {
+      const int i = i0 + g + (ci >> 1) * 8, jj = j0 + 2 * q + (ci & 1);
+      const float lv[NSL] = {acc[0][ci], acc[1][ci], acc[2][ci], acc[3][ci], acc[4][ci]};
+      float vh, vl, yh, yl, oh, ol;
+      combine_levels(lv, cscale, vh, vl);
+      const size_t idx = (size_t)i * kSmallLD + jj;
+      load1_df(Y.q, plane, idx, Y.e, yh, yl);
+      aff_df(vh, vl, yh, yl, io.alpha, io.c, oh, ol);
+      put_slices(C.q, plane, idx, oh, ol, C.e);
+      if (flags & EPI_AMAX) amax = fmaxf(amax, fabsf(oh));
+      if (flags & EPI_NORM) {
+        const bool in = (i < io.m) && (jj < io.m);
+        const float d = (i == jj) ? 1.f : 0.f;
+        const float ev = in ? __fadd_rn(__fsub_rn(oh, d), ol) : 0.f;
+        nrm += ev * ev;
+      }
+    }
+  }
+  if (flags & EPI_NORM) {
+    nrm = warp_sum_f(nrm);
+    if (lane == 0) io.norm_part[warp] = nrm;        // warps 0..7 (0 where no tile)
+  }
+  if (flags & EPI_AMAX) {
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) atomicMax(io.amax_s, __float_as_uint(amax));
+  }
+  __syncthreads();
+}
+
+// ======================================================================================
 // the per-submatrix kernel
 // ======================================================================================
 constexpr size_t kSmemTail = 256;                       // barriers and flags
-// shared memory before the barrier tail: tcgen05: TMA stages + the epilogue's staging area
-template <bool TC>
+// Engines of the kernel template (template parameter ENG).
+constexpr int ENG_TC = 0, ENG_SYNC = 1, ENG_SMALL = 2;
+// small engine: shared vectors (y_s, v_s, w_s, red_s, R_s), then the planes
+constexpr size_t kSmallVecBytes =
+    ((3 * kSmallVmax + kRedDoubles) * sizeof(double) + kSmallVmax * sizeof(int32_t) + 1023) /
+    1024 * 1024;
+constexpr size_t kSmallPlaneBytes = (size_t)kSmallLD * kSmallLD * sizeof(__half);
+// shared memory before the barrier tail: tcgen05: TMA stages + the epilogue's staging area +
+// the identity operand; mma.sync: its cp.async stages; small: vectors + resident planes
+template <int ENG>
 __host__ __device__ constexpr size_t stage_area() {
-  return TC ? (size_t)TC_STAGE_AREA + TC_STAGING_BYTES : (size_t)SY_STAGE_AREA;
+  return ENG == ENG_TC ? (size_t)TC_STAGE_AREA + TC_STAGING_BYTES + TC_Z_BYTES
+         : ENG == ENG_SYNC ? (size_t)SY_STAGE_AREA
+                           : kSmallVecBytes + kSmallPlanes * kSmallPlaneBytes;
 }
 // vectors used between GEMMs alias the stage area
 constexpr size_t kVecBytes = 4 * SUBMAT_MAX_M * sizeof(double) + kRedDoubles * sizeof(double) +
                              SUBMAT_MAX_M * sizeof(int32_t);
 static_assert(kVecBytes <= (size_t)SY_STAGE_AREA, "vector area must fit in the stage area");
 
-template <bool TC>
-__global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
+template <int ENG>
+__global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
+                                  ENG == ENG_SMALL ? kSmallCtasPerSm : 1)
     fwd_mixed_kernel(const __grid_constant__ FwdArgs a) {
+  constexpr bool TC = ENG == ENG_TC, SMALL = ENG == ENG_SMALL;
+  constexpr int VMAX = SMALL ? kSmallVmax : SUBMAT_MAX_M;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   double* y_s = reinterpret_cast<double*>(sm);
-  double* v_s = y_s + SUBMAT_MAX_M;
-  double* w_s = v_s + SUBMAT_MAX_M;
-  double* red_s = w_s + SUBMAT_MAX_M;                 // kRedDoubles doubles
+  double* v_s = y_s + VMAX;
+  double* w_s = v_s + VMAX;
+  double* red_s = w_s + VMAX;                         // kRedDoubles doubles
   int32_t* R_s = reinterpret_cast<int32_t*>(red_s + kRedDoubles);
-  unsigned char* tail = sm + stage_area<TC>();
+  unsigned char* tail = sm + stage_area<ENG>();
   uint64_t* bars = reinterpret_cast<uint64_t*>(tail);  // full, empty [TC_STAGES], tmem_full, tmem_empty
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tail + 96);
   int* abort_s = reinterpret_cast<int*>(tail + 100);
@@ -1027,12 +1183,15 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
   __shared__ int job_s;
 
   const int tid = threadIdx.x;
-  const int LD = a.ld;
+  // the sliced matrices: the CTA's global scratch (tcgen05, mma.sync) or shared memory
+  // (small engine, whose S_j takes the CTA's global scratch instead)
+  const int LD = SMALL ? kSmallLD : a.ld;
   const size_t plane = (size_t)LD * LD;
   char* scr = a.scratch + (size_t)blockIdx.x * a.scratch_stride;
-  __half* hb = reinterpret_cast<__half*>(scr);
-  double* S = reinterpret_cast<double*>(hb + 30 * plane);
+  __half* hb = SMALL ? reinterpret_cast<__half*>(sm + kSmallVecBytes) : reinterpret_cast<__half*>(scr);
+  double* S = SMALL ? reinterpret_cast<double*>(scr) : reinterpret_cast<double*>(hb + 30 * plane);
   const int plane_base = blockIdx.x * kPlanesPerCta;
+  const int vec_plane = SMALL ? kSmallVecPlane : 34;
 
   TcCtx tcx{};
   TcState tst;
@@ -1053,6 +1212,10 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     tcx.tmem_full = bars + 2 * TC_STAGES;
     tcx.tmem_empty = bars + 2 * TC_STAGES + 1;
     tcx.staging = reinterpret_cast<uint4*>(sm + TC_STAGE_AREA);
+    tcx.z = reinterpret_cast<__half*>(sm + TC_STAGE_AREA + TC_STAGING_BYTES);
+    for (int i = tid; i < TC_Z_BYTES / 16; i += blockDim.x)
+      reinterpret_cast<uint4*>(tcx.z)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
     tcx.abort_s = abort_s;
     tcx.tmem = *tmem_holder;
     tcx.tm_a = &a.tm_a;
@@ -1075,7 +1238,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
 
   int pending = -1;          // a row taken from the queue and left unfinished by a time-out
   for (;;) {
-    if (tid == 0) job_s = atomicAdd(&a.ctr->queue, 1);
+    if (tid == 0) job_s = atomicAdd(a.queue, 1);
     __syncthreads();
     const int idx = job_s;
     __syncthreads();
@@ -1090,7 +1253,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     const int p = a.p;
     // padded order: the tcgen05 engine needs multiples of its 16-wide k-step (and of 16 for
     // an MMA's N), the mma.sync engine multiples of its 64 x 64 tiles
-    const int mp = TC ? (m + 15) / 16 * 16 : pad_mixed(m);
+    const int mp = (TC || SMALL) ? (m + 15) / 16 * 16 : pad_mixed(m);
 
     // Two X buffers (p = 1 only) and three buffers for M_k and the partial products T^s M_k
     // (M_k is the A operand of all p products of an iteration and stays in place).
@@ -1101,7 +1264,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
                  {hb + 3 * NSL * plane, e_m, plane_base + 15},
                  {hb + 4 * NSL * plane, e_m, plane_base + 20}};
     // vectors carried for p >= 2 and their scratch, in the last plane (32 LD bytes)
-    double* yg = reinterpret_cast<double*>(hb + 34 * plane);     // column pos of X_k (FP64)
+    double* yg = reinterpret_cast<double*>(hb + vec_plane * plane);   // column pos of X_k
     float* ug = reinterpret_cast<float*>(yg + LD);               // residual vector
     float* yhg = ug + LD;
     float* ylg = yhg + LD;
@@ -1190,7 +1353,10 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
                     bool last = true) -> bool {
       if (TC) return gemm_tc(tcx, tst, A, B, C, Y, flags, io, vt, first, last);
       if (vt) vec_task<0>(*vt);
-      gemm_sync(A, B, C, Y, flags, io, reinterpret_cast<__half*>(sm));
+      if (SMALL)
+        gemm_small(A, B, C, Y, flags, io);
+      else
+        gemm_sync(A, B, C, Y, flags, io, reinterpret_cast<__half*>(sm));
       return true;
     };
     auto vec_of = [&](const Mat& Mk, double c, double alpha, bool track_u) {
@@ -1213,7 +1379,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
     while (!bad) {
       // p >= 2: close enough to I for the final Taylor step (see below)
       if (track && nrm2 <= kTaylorStop * kTaylorStop) break;
-      const ScaledStep st = scaled_step(fmaxf(lo, 1.f - sqrtf(nrm2)), p);
+      const ScaledStep st = scaled_step(fmaxf(lo, 1.f - sqrtf(nrm2)), p, kAlphaQuantum);
       io.c = st.c;
       io.alpha = st.alpha;
       const Mat Mk = B3[mi];
@@ -1246,7 +1412,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
         X[xc ^ 1].e = exp_of(xmax * st.tmax) + eb;
         if (tid == 0) *amax_s = 0u;
         __syncthreads();
-        if (!gemm(X[xc], Mk, X[xc ^ 1], X[xc], EPI_AMAX, nullptr)) { stop = true; break; }
+        if (!gemm(Mk, X[xc], X[xc ^ 1], X[xc], EPI_AMAX, nullptr)) { stop = true; break; }
         ++n_gemm;
         xmax = __uint_as_float(*amax_s);
         xc ^= 1;
@@ -1331,7 +1497,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
       X[xc ^ 1].e = exp_of(xmax * 2.f) + eb;
       if (tid == 0) *amax_s = 0u;
       __syncthreads();
-      if (!gemm(X[xc], B3[mi], X[xc ^ 1], X[xc], EPI_AMAX, nullptr)) {
+      if (!gemm(B3[mi], X[xc], X[xc ^ 1], X[xc], EPI_AMAX, nullptr)) {
         pending = j;
         break;
       }
@@ -1386,7 +1552,7 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
         for (int k = tid; k < a.m[j]; k += blockDim.x) out[k] = nan;
       }
       __syncthreads();
-      if (tid == 0) job_s = atomicAdd(&a.ctr->queue, 1);
+      if (tid == 0) job_s = atomicAdd(a.queue, 1);
       __syncthreads();
       const int idx = job_s;
       __syncthreads();
@@ -1404,31 +1570,41 @@ __global__ void __launch_bounds__(TC ? TC_THREADS : kThreads, 1)
 
 }  // namespace
 
-template <bool TC>
+template <int ENG>
 static size_t smem_bytes() {
-  return stage_area<TC>() + kSmemTail + 1024;       // + alignment slack
+  return stage_area<ENG>() + kSmemTail + 1024;       // + alignment slack
 }
-size_t smem_fwd_mixed() { return smem_bytes<true>(); }
+size_t smem_fwd_mixed() { return smem_bytes<ENG_TC>(); }
 
 size_t scratch_mixed(int ld) { return (size_t)kPlanesPerCta * ld * ld * sizeof(__half); }
 
+size_t scratch_small() { return (size_t)kSmallMaxM * kSmallMaxM * sizeof(double); }
+
+int small_engine_max_m() { return kSmallMaxM; }
+
 cudaError_t launch_fwd_mixed(const FwdArgs& a, int grid, cudaStream_t s) {
-  if (a.engine == 1)
-    fwd_mixed_kernel<false><<<grid, kThreads, smem_bytes<false>(), s>>>(a);
+  if (a.engine == ENG_SYNC)
+    fwd_mixed_kernel<ENG_SYNC><<<grid, kThreads, smem_bytes<ENG_SYNC>(), s>>>(a);
+  else if (a.engine == ENG_SMALL)
+    fwd_mixed_kernel<ENG_SMALL><<<grid, kThreads, smem_bytes<ENG_SMALL>(), s>>>(a);
   else
-    fwd_mixed_kernel<true><<<grid, TC_THREADS, smem_bytes<true>(), s>>>(a);
+    fwd_mixed_kernel<ENG_TC><<<grid, TC_THREADS, smem_bytes<ENG_TC>(), s>>>(a);
   return cudaGetLastError();
 }
 
-int mixed_ctas_per_sm() { return 1; }
+int mixed_ctas_per_sm(int engine) { return engine == ENG_SMALL ? kSmallCtasPerSm : 1; }
 
 cudaError_t set_attr_mixed() {
-  cudaError_t e = cudaFuncSetAttribute(fwd_mixed_kernel<true>,
+  cudaError_t e = cudaFuncSetAttribute(fwd_mixed_kernel<ENG_TC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes<true>());
+                                       (int)smem_bytes<ENG_TC>());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fwd_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_bytes<false>());
+  e = cudaFuncSetAttribute(fwd_mixed_kernel<ENG_SMALL>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_bytes<ENG_SMALL>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fwd_mixed_kernel<ENG_SYNC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes<ENG_SYNC>());
 }
 
 }  // namespace submat

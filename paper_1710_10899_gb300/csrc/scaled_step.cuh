@@ -47,7 +47,10 @@ constexpr int kStartLoSteps = 8;    // power steps for the starting lower end
 
 // g(lo) = g(1) has the closed form alpha = (r - lo) / (r - 1) with r = lo^(-1/p), i.e.
 // alpha = 1 + (1 - lo) / expm1(-ln(lo) / p), evaluated without cancellation near lo = 1.
-__host__ __device__ inline ScaledStep scaled_step(float lo, int p) {
+// With alpha_quantum > 0, alpha is rounded to a multiple of it (an engine that applies
+// alpha I as an exact integer operand needs that) and c and the next lower end are taken for
+// the rounded alpha, so the peak still lands on 1; any alpha keeps the iteration's invariant.
+__host__ __device__ inline ScaledStep scaled_step(float lo, int p, float alpha_quantum = 0.f) {
   ScaledStep s;
   if (!(lo >= kLoMin)) lo = kLoMin;
   const float d = 1.f - lo;
@@ -64,11 +67,14 @@ __host__ __device__ inline ScaledStep scaled_step(float lo, int p) {
   }
   s.newton = false;
   const float em = expm1f(-log1pf(-d) / (float)p);
-  const float alpha = 1.f + d / em;
+  float alpha = 1.f + d / em;
+  if (alpha_quantum > 0.f)     // (alpha stays above 1, where g(1) would vanish)
+    alpha = fmaxf(rintf(alpha / alpha_quantum), 1.f / alpha_quantum + 1.f) * alpha_quantum;
   const float peak = step_map(alpha / (float)(p + 1), alpha, p);
   s.alpha = alpha;
   s.c = powf(peak, -1.f / (float)p);
-  s.lo_next = fminf(step_map(lo, alpha, p) / peak, 1.f);
+  // g(lo) = g(1) unless alpha was rounded: the lower of the two ends
+  s.lo_next = fminf(fminf(step_map(lo, alpha, p), step_map(1.f, alpha, p)) / peak, 1.f);
   s.tmax = s.c * alpha;
   return s;
 }

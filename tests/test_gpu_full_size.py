@@ -6,7 +6,8 @@
   the FP64 oracle at 1e-6;
 * the differentiation workload, n = 16384: the adjoint against the oracle's gradient over
   every stored entry (1e-10) and against central differences (step 1e-6, FP64 forward) on
-  32 random sparse symmetric directions of unit norm (seed 2).
+  32 random sparse symmetric directions of unit norm (seeds 2000..2031), each error at most
+  1e-6 of the directions' RMS derivative.
 
 The oracle runs in spawned worker processes on the host cores (this process has already
 made CUDA calls, so it must not fork).
@@ -84,12 +85,17 @@ def test_adjoint_stated_size(sm):
         return float(torch.dot(w, y))
 
     h = 1e-6
-    rel = []
+    fd, ad = [], []
     for k in range(32):
-        e = torch.tensor(wl.random_on_pattern(a, seed=1000 * 2 + k, symmetric=True), device="cuda")
+        e = torch.tensor(wl.random_on_pattern(a, seed=2000 + k, symmetric=True), device="cuda")
         e /= e.norm()
-        fd = (loss(base + h * e) - loss(base - h * e)) / (2 * h)
-        ad = float(torch.dot(g, e))
-        rel.append(abs(fd - ad) / abs(ad))
-    rel = np.array(rel)
-    assert rel.max() <= 1e-6, rel
+        fd.append((loss(base + h * e) - loss(base - h * e)) / (2 * h))
+        ad.append(float(torch.dot(g, e)))
+    fd, ad = np.array(fd), np.array(ad)
+    # The forward's FP64 rounding leaves ~1e-15 relative noise in L, i.e. ~1e-13 absolute,
+    # which the step turns into ~1e-7 of a typical directional derivative; a direction
+    # whose derivative happens to be small would magnify it.  Each error is therefore
+    # measured against the directions' RMS derivative.
+    scale = float(np.sqrt(np.mean(ad ** 2)))
+    err = np.abs(fd - ad) / scale
+    assert err.max() <= 1e-6, (err.max(), err, ad)
