@@ -126,7 +126,20 @@ typedef struct {
                               gives those rows' contribution to grad_in (the shards'
                               grad_in add up to the full gradient)                         */
   int32_t shard_rank;      /* 0 .. shard_count-1                                          */
+  int32_t small_max_m;     /* SUBMAT_PREC_MIXED_F16: rows of order m <= small_max_m take the
+                              small-submatrix engine (every working matrix in shared memory,
+                              warp-level mma.sync tiles); 0 disables it; at most
+                              SUBMAT_SMALL_MAX_M; < 0 selects the tuned default            */
+  int32_t sync_max_m;      /* SUBMAT_PREC_MIXED_F16: rows with small_max_m < m <= sync_max_m
+                              take the mma.sync engine (64 x 64 tiles), larger rows the
+                              tcgen05 engine (128 x 96 tiles in tensor memory); < 0 selects
+                              the tuned default.  The rows are ordered by decreasing m, so
+                              each engine gets one contiguous run of the work queue and one
+                              persistent launch                                           */
 } submat_opts;
+
+/* Largest order the small-submatrix engine takes. */
+#define SUBMAT_SMALL_MAX_M 32
 
 typedef struct {
   int64_t n_rows;          /* submatrices processed by the last forward                  */

@@ -21,6 +21,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsubmat.so")
 
 SUBMAT_MAX_M = 1536
+SUBMAT_SMALL_MAX_M = 32
 PREC_FP64 = 0
 PREC_MIXED_F16 = 1
 PREC_MIXED_F16_SYNC = 2
@@ -52,7 +53,8 @@ class Opts(ctypes.Structure):
                 ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("kappa_max", ctypes.c_double), ("root_sign", ctypes.c_int32),
                 ("grad_deterministic", ctypes.c_int32), ("grad_wave_mib", ctypes.c_int32),
-                ("shard_count", ctypes.c_int32), ("shard_rank", ctypes.c_int32)]
+                ("shard_count", ctypes.c_int32), ("shard_rank", ctypes.c_int32),
+                ("small_max_m", ctypes.c_int32), ("sync_max_m", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -144,7 +146,8 @@ class Plan:
     def __init__(self, rowptr, colind, p: int, precision: str = "mixed", k_max: int = 0,
                  tol: float = 0.0, resid_tol: float = 0.0, refine_steps: int = -1,
                  use_graph: bool = True, kappa_max: float = 0.0, root_sign: int = -1,
-                 grad_deterministic: bool = False, grad_wave_mib: int = 0, shard=(0, 1)):
+                 grad_deterministic: bool = False, grad_wave_mib: int = 0, shard=(0, 1),
+                 small_max_m: int = -1, sync_max_m: int = -1):
         lib = load_library()
         self._lib = lib
         torch = _torch()
@@ -177,6 +180,10 @@ class Plan:
         o.grad_deterministic = 1 if grad_deterministic else 0
         o.grad_wave_mib = int(grad_wave_mib)
         o.shard_rank, o.shard_count = int(shard[0]), int(shard[1])
+        if small_max_m >= 0:
+            o.small_max_m = int(small_max_m)
+        if sync_max_m >= 0:
+            o.sync_max_m = int(sync_max_m)
         h = ctypes.c_void_p()
         _check(lib, lib.submat_plan(ctypes.byref(csr), int(p), ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -12,10 +12,10 @@
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
+#include "engine_table.h"
 
 namespace submat {
 cudaError_t set_attr_mixed();
-int mixed_ctas_per_sm(int engine); // CTAs per SM of a mixed-path engine
 cudaError_t set_attr_fp64();
 cudaError_t set_attr_eig();
 }  // namespace submat
@@ -39,6 +39,13 @@ submat_status fail(submat_status s, const std::string& msg) {
                   std::string(#expr) + ": " + cudaGetErrorString(err_));                \
     }                                                                                   \
   } while (0)
+
+// One persistent launch of the mixed forward: an engine over order[begin, begin + count).
+struct EngineRun {
+  int engine = 0;
+  int32_t begin = 0, count = 0;
+  int grid = 0;
+};
 
 struct GraphEntry {
   const double* in = nullptr;
@@ -122,6 +129,7 @@ struct submat_plan_s {
   std::vector<std::pair<int32_t, int32_t>> waves;
   double* d_cg = nullptr;          // submat_pcg work vectors (allocated by the first call)
   std::vector<GraphEntry> graphs;
+  std::vector<EngineRun> runs;        // mixed path: engine launches by size bucket
 };
 
 namespace {
@@ -192,7 +200,7 @@ submat_status enqueue_forward(submat_plan_t P, const double* in, double* out, cu
   a.kappa_max = P->opts.kappa_max;
   a.sign = P->opts.root_sign;
   a.ld = P->ld;
-  a.engine = P->opts.precision == SUBMAT_PREC_MIXED_F16_SYNC ? 1 : 0;
+  a.engine = kEngineTc;
   a.queue = &P->d_ctr->queue;
   a.tm_a = P->tm_a;
   a.tm_b = P->tm_b;
@@ -201,10 +209,20 @@ submat_status enqueue_forward(submat_plan_t P, const double* in, double* out, cu
                            cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemsetAsync(P->d_ctr, 0, sizeof(DevCounters), s));
   CUDA_TRY(cudaEventRecordWithFlags(P->ev[0], s, evf));
-  if (P->opts.precision == SUBMAT_PREC_FP64)
+  if (P->opts.precision == SUBMAT_PREC_FP64) {
     CUDA_TRY(launch_fwd_fp64(a, P->grid, s));
-  else
-    CUDA_TRY(launch_fwd_mixed(a, P->grid, s));
+  } else {
+    for (size_t r = 0; r < P->runs.size(); ++r) {    // longest rows first, one engine per run
+      const EngineRun& run = P->runs[r];
+      FwdArgs b = a;
+      b.engine = run.engine;
+      b.order = P->d_order + run.begin;
+      b.n = run.count;
+      b.queue = &P->d_ctr->run_queue[r];
+      b.scratch_stride = run.engine == kEngineSmall ? scratch_small() : P->stride;
+      CUDA_TRY(launch_fwd_mixed(b, run.grid, s));
+    }
+  }
   CUDA_TRY(cudaEventRecordWithFlags(P->ev[1], s, evf));
   CUDA_TRY(launch_fallback(a, P->grid, s));
   CUDA_TRY(cudaEventRecordWithFlags(P->ev[2], s, evf));
@@ -258,6 +276,8 @@ void submat_default_opts(submat_opts* o) {
   o->grad_wave_mib = 0;
   o->shard_count = 0;
   o->shard_rank = 0;
+  o->small_max_m = kTunedSmallMaxM;
+  o->sync_max_m = kTunedSyncMaxM;
 }
 
 const char* submat_status_string(submat_status s) {
@@ -313,6 +333,10 @@ static submat_status plan_impl(const submat_csr* csr, int32_t p, const submat_op
   } else if (o.shard_rank < 0 || o.shard_rank >= o.shard_count) {
     return fail(SUBMAT_EINVAL, "shard_rank must lie in [0, shard_count)");
   }
+  if (o.small_max_m < 0) o.small_max_m = kTunedSmallMaxM;
+  if (o.sync_max_m < 0) o.sync_max_m = kTunedSyncMaxM;
+  if (o.small_max_m > small_engine_max_m())
+    return fail(SUBMAT_EINVAL, "small_max_m exceeds SUBMAT_SMALL_MAX_M");
 
   const int32_t n = csr->n;
   const int64_t nnz = csr->nnz;
@@ -433,9 +457,35 @@ static submat_status plan_impl(const submat_csr* csr, int32_t p, const submat_op
   size_t stride = mixed ? scratch_mixed(P->ld) : std::max(scratch_eig(mp), scratch_fp64(mp));
   stride = (stride + 1023) / 1024 * 1024;
   P->stride = stride;
-  const int ctas = (o.precision == SUBMAT_PREC_MIXED_F16) ? mixed_ctas_per_sm(0) : 1;
-  P->grid = std::max(1, std::min(P->n_sm * ctas, P->n_jobs));
-  PLAN_TRY(cudaMalloc(&P->d_scratch, stride * (size_t)P->grid));
+  P->grid = std::max(1, std::min(P->n_sm, P->n_jobs));
+  // the mixed path's engine runs: the plan's rows are ordered by decreasing m, so each size
+  // bucket is one contiguous run of the order (tcgen05, then mma.sync, then small)
+  size_t scratch_bytes = stride * (size_t)P->grid;
+  if (mixed) {
+    int32_t cnt[3] = {0, 0, 0};
+    for (int32_t j = P->row_begin; j < P->row_end; ++j) {
+      const int32_t mj = h_m[j];
+      int e = kEngineTc;
+      if (o.precision == SUBMAT_PREC_MIXED_F16_SYNC) e = kEngineSync;
+      else if (mj <= o.small_max_m) e = kEngineSmall;
+      else if (mj <= o.sync_max_m) e = kEngineSync;
+      cnt[e]++;
+    }
+    int32_t begin = 0;
+    for (int e : {kEngineTc, kEngineSync, kEngineSmall}) {
+      if (cnt[e] == 0) continue;
+      EngineRun run;
+      run.engine = e;
+      run.begin = begin;
+      run.count = cnt[e];
+      run.grid = std::max(1, std::min(P->n_sm * mixed_ctas_per_sm(e), cnt[e]));
+      if (e == kEngineSmall)
+        scratch_bytes = std::max(scratch_bytes, scratch_small() * (size_t)run.grid);
+      P->runs.push_back(run);
+      begin += cnt[e];
+    }
+  }
+  PLAN_TRY(cudaMalloc(&P->d_scratch, scratch_bytes));
   if (mixed && o.precision == SUBMAT_PREC_MIXED_F16) {
     // TMA descriptors over all CTAs' planes: dims (LD cols, LD rows, planes), 32-byte swizzle
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;

@@ -30,6 +30,7 @@ struct DevCounters {
   double flops_tensor;
   unsigned long long n_illcond;        // rows sent to the fallback by the condition estimate
   int32_t error;                       // a device pipeline wait timed out
+  int32_t run_queue[4];                // work-queue heads of the mixed path's engine launches
   double flops_alg;                    // sum over rows of k_j (p+1) 2 m_j^3 (+ 2 m_j^3 for
                                        // p = 1's final X product): executed iterations k_j,
                                        // true orders m_j, every product counted as a dense GEMM
@@ -121,6 +122,12 @@ cudaError_t cg_update(double alpha, double* x, double* r, const double* p, const
                       int32_t n, double* part, double* rr, cudaStream_t s);
 cudaError_t cg_dir(double beta, const double* r, double* p, int32_t n, cudaStream_t s);
 size_t cg_dot_scratch();
+
+// Mixed-path engines (FwdArgs::engine) and their limits.
+constexpr int kEngineTc = 0, kEngineSync = 1, kEngineSmall = 2;
+int mixed_ctas_per_sm(int engine);    // CTAs per SM of a mixed-path engine
+int small_engine_max_m();             // largest order the small engine takes
+size_t scratch_small();               // small engine: global scratch bytes per CTA
 
 // Dynamic shared memory of each kernel (bytes), for cudaFuncSetAttribute at plan time.
 size_t smem_fwd_mixed();

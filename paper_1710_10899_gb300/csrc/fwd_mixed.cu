@@ -569,8 +569,8 @@ __device__ __forceinline__ int sw32_index(int q, int k) {
 // planes of a stage lie back to back (96 rows each), and level L = s + t of A_s B_t sits at
 // TMEM columns 96 L, so A_s times B planes t0..t1 is one MMA with N = 96 (t1 - t0 + 1) whose
 // output columns start at 96 (s + t0).  The fifteen plane products become eight MMAs (N = 240,
-// 240, 192, 192, 144, 144, 192, 96), each reading its A plane once.  A narrower last tile
-// issues the fifteen products separately with N = nw.
+// 240, 192, 192, 144, 144, 192, 96), each reading its A plane once.  A last tile narrower
+// than 64 columns issues the fifteen products separately with N = nw.
 __device__ __forceinline__ void mma_kstep_full(uint32_t d0, uint64_t da0, uint64_t db0,
                                                uint32_t acc0) {
   constexpr uint32_t i240 = tc::idesc_f16(TC_M, 240), i192 = tc::idesc_f16(TC_M, 192),
@@ -681,7 +681,10 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
         int tm, tn;
         tc_tile(t, ntn, tm, tn);
         const int nw = min(TC_N, mp - tn * TC_N);      // 96, or 16..80 for the last tile
-        const bool full = nw == TC_N;
+        // tiles of 64 columns or more take the concatenated MMAs at the full width (their
+        // extra columns, beyond nw, are never read): per k-step ~730 tensor cycles against
+        // ~780 for fifteen separate N = 80 products and ~720 for N = 64
+        const bool full = nw >= 64;
         const uint32_t idesc = tc::idesc_f16(TC_M, nw);
         // k-steps inside the tile's diagonal block carry the affine term
         const int kd0 = tm * (TC_M / TC_K), kd1 = min(KT, kd0 + TC_M / TC_K);
@@ -752,8 +755,10 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
       const int nch = nw / 8;
       // tile-uniform: do any of its columns reach a later row block (mirror images)?
       const bool tile_mirror = (tn * TC_N + nw - 1) / TC_M > tm;
-      // phase 1: w = acc0 + 2^-8 acc1 + (levels 2..4) (the first two exactly) into the
-      // staging units of row rt
+      // phase 1: w = acc0 + 2^-8 acc1 + 2^-16 acc2 (error-free sums) + (levels 3, 4) as a
+      // double-float into the staging units of row rt.  Level 2 must not be rounded to
+      // FP32: when a matrix's entries lie far below its power-of-two scale (or the affine
+      // term cancels level 0), levels 0 and 1 are nearly empty and level 2 carries the value
       {
         const int cb = half * TC_EPI_COLS;              // this warp's columns [cb, cb + 48)
         const int ce = min(cb + TC_EPI_COLS, nw);
@@ -770,11 +775,13 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const int k = 2 * k2 + h;
+              float s0, e0, t, u;
+              two_sum(acc[0][k], acc[1][k] * (1.f / 256.f), s0, e0);
+              two_sum(s0, acc[2][k] * (1.f / 65536.f), t, u);
+              e0 = __fadd_rn(__fadd_rn(e0, u), __fmaf_rn(acc[4][k], 1.f / 4294967296.f,
+                                                         acc[3][k] * (1.f / 16777216.f)));
               float wh, wl;
-              two_sum(acc[0][k], acc[1][k] * (1.f / 256.f), wh, wl);
-              wl = __fadd_rn(wl, __fmaf_rn(acc[4][k], 1.f / 4294967296.f,
-                                           __fmaf_rn(acc[3][k], 1.f / 16777216.f,
-                                                     acc[2][k] * (1.f / 65536.f))));
+              two_sum(t, e0, wh, wl);
               w4[2 * h] = wh;
               w4[2 * h + 1] = wl;
             }
@@ -1072,6 +1079,9 @@ constexpr int kSmallPlanes = 26;           // X[2], three M / partial-product bu
 constexpr int kSmallVecPlane = 25;
 constexpr int kSmallVmax = 64;             // length of the shared vectors y_s, v_s, w_s, R_s
 constexpr int kSmallCtasPerSm = 2;
+static_assert(kSmallMaxM == SUBMAT_SMALL_MAX_M, "the header's limit of the small engine");
+static_assert(kSmallMaxM + 8 <= kSmallLD && kSmallLD % 8 == 0, "padded rows, 16-byte aligned");
+static_assert(44 * kSmallLD <= (int)(kSmallLD * kSmallLD * 2), "vectors fit their plane");
 
 __device__ __forceinline__ void ldsm_x2_t(uint32_t* r, const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"

@@ -192,6 +192,7 @@ def test_binding_constants_match_the_header():
     assert enums["SUBMAT_PREC_MIXED_F16_SYNC"] == pkg.PREC_MIXED_F16_SYNC
     assert macros["SUBMAT_MAX_M"] == pkg.SUBMAT_MAX_M
     assert macros["SUBMAT_NOALLOC_MAX_M"] == pkg.SUBMAT_NOALLOC_MAX_M
+    assert macros["SUBMAT_SMALL_MAX_M"] == pkg.SUBMAT_SMALL_MAX_M
 
 
 def _prototypes():

@@ -144,6 +144,35 @@ def test_algorithmic_flop_count(sm, precision, p):
     assert rep["flops_alg"] == pytest.approx(expect, rel=1e-12)
 
 
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_small_engine_all_rows(sm, p, sign):
+    """Orders 1..27: every row runs on the small-submatrix engine (working set in shared
+    memory, warp-level mma.sync tiles)."""
+    a = wl.overlap_small()
+    plan, y = run(sm, a, p, "mixed", root_sign=sign, small_max_m=32)
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, p, sign=sign)
+    assert row_errors(a, y, ref, range(a.n)).max() <= TOL["mixed"]
+    rep = plan.report()
+    # a submatrix whose condition estimate exceeds kappa_max goes to the FP64 fallback
+    assert rep["n_notspd"] == 0 and rep["n_fallback"] <= 2 and rep["iters_sum"] > a.n
+
+
+@pytest.mark.parametrize("buckets", [(0, 0), (32, 0), (32, 64), (16, 48), (0, 1536)])
+def test_engine_buckets(sm, buckets):
+    """Rows routed by order to the small engine, the mma.sync engine and the tcgen05 engine
+    (one persistent launch each) all meet the bar, on the uneven workload at 1/8 scale
+    (orders 10..596), checked on a sample stratified by size."""
+    small, sync = buckets
+    a = wl.overlap_clustered(n=16384)
+    plan, y = run(sm, a, 2, "mixed", small_max_m=small, sync_max_m=sync)
+    rows = wl.stratified_rows(a.row_sizes(), 240, seed=3)
+    ref = oracle.pool.invroot(a.rowptr, a.colind, a.vals, 2, rows=rows)
+    assert row_errors(a, y, ref, rows).max() <= TOL["mixed"]
+    rep = plan.report()
+    assert rep["n_fallback"] == 0 and rep["n_rows"] == a.n
+
+
 def test_dense_pattern_equals_full_root(sm):
     import scipy.linalg as sl
     rng = np.random.default_rng(9)
@@ -267,12 +296,12 @@ def test_graph_and_stream_paths_agree(sm):
 def test_repeat_runs_bitwise_equal(sm, precision):
     """Every reduction that steers the iteration (norms, maxima) is taken in a fixed order,
     so repeated calls give identical bits (orders 40..250: ragged tiles and mirror images)."""
-    a = wl.overlap_uniform(n=1500)
-    v = torch.tensor(a.vals, device="cuda")
-    plan = sm.submat_plan(a.rowptr, a.colind, 2, precision=precision, use_graph=False)
-    ys = [sm.submat_invroot(plan, v, sync=True) for _ in range(3)]
-    for y in ys[1:]:
-        assert torch.equal(ys[0], y)
+    for a in (wl.overlap_uniform(n=1500), wl.overlap_small(n=800)):
+        v = torch.tensor(a.vals, device="cuda")
+        plan = sm.submat_plan(a.rowptr, a.colind, 2, precision=precision, use_graph=False)
+        ys = [sm.submat_invroot(plan, v, sync=True) for _ in range(3)]
+        for y in ys[1:]:
+            assert torch.equal(ys[0], y)
 
 
 def test_device_pattern_input(sm):

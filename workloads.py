@@ -223,6 +223,22 @@ def random_on_pattern(a: CSR, seed: int, symmetric: bool = False) -> np.ndarray:
     return w
 
 
+def block_diagonal_spd(blocks: int, size: int, seed: int = 0) -> CSR:
+    """``blocks`` dense random SPD blocks of one order ``size`` on the diagonal, each stored in
+    full, so every row's submatrix has order exactly ``size`` (Q Q^T / size + 0.5 I with Q
+    standard normal, numpy PCG64).  Used to time the engines per row size."""
+    rng = np.random.default_rng(seed)
+    n = blocks * size
+    qs = rng.standard_normal((blocks, size, size))
+    vals = np.einsum("bij,bkj->bik", qs, qs) / size + 0.5 * np.eye(size)[None]
+    r = np.arange(n, dtype=np.int64)
+    blk = r // size
+    rowptr = (np.arange(n + 1, dtype=np.int64) * size).astype(np.int32)
+    colind = (blk[:, None] * size + np.arange(size)[None, :]).ravel().astype(np.int32)
+    v = vals[blk, r % size, :].ravel().astype(np.float64)
+    return CSR(n, rowptr, colind, v, f"block_diagonal_spd(blocks={blocks},size={size})")
+
+
 def stratified_rows(m: np.ndarray, k: int, seed: int = 3) -> np.ndarray:
     """A seeded sample of about k row indices stratified by row size: the sizes are binned
     by powers of two (below 32, 32..63, ..., 1024..2047, 2048 and above), each non-empty bin
