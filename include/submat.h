@@ -257,6 +257,28 @@ SUBMAT_API submat_status submat_pcg(submat_plan_t plan, const double* vals_a, co
                                     const double* b, double* x, double tol, int32_t max_iter,
                                     int32_t* iters, double* rel_resid, void* stream);
 
+/*
+ * Global refinement of an approximate inverse p-th root on the plan's pattern (Sec. 4.5:
+ * the submatrix method's result as the starting guess of a Newton iteration for A^(-1/p),
+ * every product restricted to the pattern as a sparse iteration has to be).  From the
+ * symmetric part X of x_in, `iters` steps of
+ *     R = A X, then R <- R X (p - 1 more times);  X <- ((p + 1) X - X R) / p;
+ *     X <- (X + X^T) / 2,
+ * each product C = L R restricted to the pattern: C[i][j] = sum over k with (i, k) and
+ * (k, j) stored of L[i][k] R[k][j], for every stored (i, j).  FP64, a fixed summation order
+ * (identical bits on every call).  a_vals, x_in, x_out: device arrays of nnz doubles on the
+ * plan's pattern (A's values and the start, e.g. the result of submat_invroot; on a pattern
+ * wider than A's, such as that of A^2, A's values are zero where A stores nothing); x_out may
+ * alias x_in.  The plan's p and precision are not used.  Synchronous on the stream; work
+ * arrays of 4 nnz doubles (and the plan's transposed map) are allocated by the first call.
+ * The step converges only from a start that commutes with A closely enough: for p = 1
+ * (Newton-Schulz for the inverse) the error E maps to -E A E, for p >= 2 error components
+ * that couple eigenvalues far apart grow.
+ */
+SUBMAT_API submat_status submat_refine(submat_plan_t plan, const double* a_vals,
+                                       const double* x_in, int32_t p, int32_t iters,
+                                       double* x_out, void* stream);
+
 /* Counters of the last forward (synchronises the plan's stream). */
 SUBMAT_API submat_status submat_get_report(submat_plan_t plan, submat_report* out);
 
@@ -268,12 +290,13 @@ SUBMAT_API submat_status submat_plan_rows(submat_plan_t plan, int32_t* m, int32_
 
 /*
  * Test aid for the bounded device waits (the paper has no counterpart).  While on != 0,
- * every CTA of the plan's tensor-core forward (SUBMAT_PREC_MIXED_F16) first waits on a
- * pipeline barrier that nothing signals, before it issues any copy or tensor-core operation;
- * the wait gives up after its poll limit (on the order of a second), the CTA writes NaN to
- * every row it takes from the work queue, and submat_invroot returns SUBMAT_ETIMEOUT (with
- * sync != 0; submat_get_report still works).  on = 0 restores normal operation.  Other
- * precisions ignore the flag.  Synchronises the device.
+ * every CTA of the plan's tcgen05 engine launch (SUBMAT_PREC_MIXED_F16, rows above the
+ * small and mma.sync buckets) first waits on a pipeline barrier that nothing signals, before
+ * it issues any copy or tensor-core operation; the wait gives up after its poll limit (on
+ * the order of a second), the CTA writes NaN to every row it takes from its work queue, and
+ * submat_invroot returns SUBMAT_ETIMEOUT (with sync != 0; submat_get_report still works).
+ * Rows of the other engines are computed as usual.  on = 0 restores normal operation.
+ * Other precisions ignore the flag.  Synchronises the device.
  */
 SUBMAT_API submat_status submat_test_stall(submat_plan_t plan, int32_t on);
 

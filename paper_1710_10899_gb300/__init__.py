@@ -74,7 +74,7 @@ EXPORTS = ["submat_default_opts", "submat_plan", "submat_invroot", "submat_invro
            "submat_invroot_backward",
            "submat_get_report", "submat_plan_rows", "submat_plan_shape", "submat_plan_destroy",
            "submat_status_string", "submat_last_error", "submat_invroot_noalloc", "submat_pcg",
-           "submat_shard_rows", "submat_test_stall"]
+           "submat_shard_rows", "submat_test_stall", "submat_refine"]
 
 _lib_handle = None
 
@@ -119,6 +119,8 @@ def load_library(path: str = LIB_PATH):
     lib.submat_shard_rows.restype = i32
     lib.submat_test_stall.argtypes = [vp, i32]
     lib.submat_test_stall.restype = i32
+    lib.submat_refine.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+    lib.submat_refine.restype = i32
     _lib_handle = lib
     return lib
 
@@ -305,6 +307,22 @@ def submat_pcg(plan: Plan, vals_a, b=None, vals_k=None, tol: float = 1e-6, max_i
         ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), float(tol), int(max_iter),
         ctypes.byref(it), ctypes.byref(rel), _stream_ptr(stream)))
     return x, int(it.value), float(rel.value)
+
+
+def submat_refine(plan: Plan, a_vals, x_in, p: int, iters: int, x_out=None, stream=None):
+    """``submat_refine``: ``iters`` Newton steps for A^(-1/p) from the symmetric part of
+    ``x_in``, every product restricted to the plan's pattern (Sec. 4.5).  ``a_vals`` and
+    ``x_in`` are CUDA float64 tensors of the pattern's nnz values."""
+    torch = _torch()
+    av = plan._vals(a_vals)
+    xv = plan._vals(x_in)
+    if x_out is None:
+        x_out = torch.empty_like(xv)
+    _check(plan._lib, plan._lib.submat_refine(plan._h, ctypes.c_void_p(av.data_ptr()),
+                                              ctypes.c_void_p(xv.data_ptr()), int(p), int(iters),
+                                              ctypes.c_void_p(x_out.data_ptr()),
+                                              _stream_ptr(stream)))
+    return x_out
 
 
 def shard_rows(rowptr, count: int, rank: int):

@@ -14,7 +14,8 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libsubmat.so")
 BUILD_DIR = os.path.join(PKG, "_build")
 NVCC = os.environ.get("NVCC", "nvcc")
-SOURCES = ["api.cu", "plan.cu", "fwd_mixed.cu", "fwd_fp64.cu", "eig.cu", "noalloc.cu", "cg.cu"]
+SOURCES = ["api.cu", "plan.cu", "fwd_mixed.cu", "fwd_fp64.cu", "eig.cu", "noalloc.cu", "cg.cu",
+           "refine_global.cu"]
 FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",

@@ -128,6 +128,7 @@ struct submat_plan_s {
   double* d_gbuf = nullptr;
   std::vector<std::pair<int32_t, int32_t>> waves;
   double* d_cg = nullptr;          // submat_pcg work vectors (allocated by the first call)
+  double* d_ref = nullptr;         // submat_refine work arrays (allocated by the first call)
   std::vector<GraphEntry> graphs;
   std::vector<EngineRun> runs;        // mixed path: engine launches by size bucket
 };
@@ -150,6 +151,7 @@ void release(submat_plan_t P) {
   cudaFree(P->d_gofs);
   cudaFree(P->d_gbuf);
   cudaFree(P->d_cg);
+  cudaFree(P->d_ref);
   cudaFree(P->d_rowptr);
   cudaFree(P->d_colind);
   cudaFree(P->d_m);
@@ -763,6 +765,48 @@ static submat_status pcg_impl(submat_plan_t P, const double* vals_a, const doubl
   return st;
 }
 
+static submat_status refine_impl(submat_plan_t P, const double* a_vals, const double* x_in,
+                                 int32_t p, int32_t iters, double* x_out, void* stream) {
+  g_last_error.clear();
+  if (!P) return fail(SUBMAT_EINVAL, "plan is NULL");
+  if (!a_vals || !x_in || !x_out) return fail(SUBMAT_EINVAL, "NULL array");
+  if (p < 1 || iters < 0) return fail(SUBMAT_EINVAL, "p must be >= 1 and iters >= 0");
+  if (P->n == 0) return SUBMAT_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  DeviceScope dev;
+  CUDA_TRY(dev.enter(P->device));
+  const int64_t nnz = P->nnz;
+  if (!P->d_ref) CUDA_TRY(cudaMalloc(&P->d_ref, 4 * (size_t)nnz * sizeof(double)));
+  CUDA_TRY(ensure_tpos(P, s));
+  double* x = P->d_ref;              // the iterate
+  double* r = x + nnz;               // R = A X^i
+  double* t = r + nnz;               // transposed values
+  double* c = t + nnz;               // a restricted product
+  const int32_t* rp = P->d_rowptr;
+  const int32_t* ci = P->d_colind;
+  // X = (X0 + X0^T) / 2
+  CUDA_TRY(cg_transpose_vals(rp, ci, P->d_tpos, x_in, t, nnz, s));
+  CUDA_TRY(refine_axpby(0.5, x_in, 0.5, t, x, nnz, s));
+  for (int32_t it = 0; it < iters; ++it) {
+    // R = A X (X symmetric: X^T's values are X's), then R <- R X, p - 1 times
+    CUDA_TRY(refine_masked_product(rp, ci, P->n, a_vals, x, r, s));
+    for (int32_t k = 1; k < p; ++k) {
+      CUDA_TRY(refine_masked_product(rp, ci, P->n, r, x, c, s));
+      CUDA_TRY(cudaMemcpyAsync(r, c, (size_t)nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    // X <- ((p + 1) X - X R) / p, then X <- (X + X^T) / 2
+    CUDA_TRY(cg_transpose_vals(rp, ci, P->d_tpos, r, t, nnz, s));
+    CUDA_TRY(refine_masked_product(rp, ci, P->n, x, t, c, s));
+    CUDA_TRY(refine_axpby((double)(p + 1) / p, x, -1.0 / p, c, c, nnz, s));
+    CUDA_TRY(cg_transpose_vals(rp, ci, P->d_tpos, c, t, nnz, s));
+    CUDA_TRY(refine_axpby(0.5, c, 0.5, t, x, nnz, s));
+  }
+  CUDA_TRY(cudaMemcpyAsync(x_out, x, (size_t)nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  P->last_stream = s;
+  return SUBMAT_OK;
+}
+
 submat_status submat_get_report(submat_plan_t P, submat_report* r) {
   g_last_error.clear();
   if (!P || !r) return fail(SUBMAT_EINVAL, "NULL argument");
@@ -839,6 +883,11 @@ submat_status submat_invroot_host(submat_plan_t P, const double* in, double* out
 submat_status submat_invroot_backward(submat_plan_t P, const double* grad_out, double* grad_in,
                                       void* stream) {
   SUBMAT_NOTHROW(backward_impl(P, grad_out, grad_in, stream))
+}
+
+submat_status submat_refine(submat_plan_t P, const double* a_vals, const double* x_in, int32_t p,
+                            int32_t iters, double* x_out, void* stream) {
+  SUBMAT_NOTHROW(refine_impl(P, a_vals, x_in, p, iters, x_out, stream))
 }
 
 submat_status submat_pcg(submat_plan_t P, const double* vals_a, const double* vals_k,

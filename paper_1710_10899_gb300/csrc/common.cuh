@@ -123,6 +123,13 @@ cudaError_t cg_update(double alpha, double* x, double* r, const double* p, const
 cudaError_t cg_dir(double beta, const double* r, double* p, int32_t n, cudaStream_t s);
 size_t cg_dot_scratch();
 
+// Global refinement pieces (refine_global.cu): C = (L R) restricted to the pattern, R given
+// through R^T's values on the (symmetric) pattern; out = c1 x + c2 y.
+cudaError_t refine_masked_product(const int32_t* rowptr, const int32_t* colind, int32_t n,
+                                  const double* L, const double* Rt, double* C, cudaStream_t s);
+cudaError_t refine_axpby(double c1, const double* x, double c2, const double* y, double* out,
+                         int64_t nnz, cudaStream_t s);
+
 // Mixed-path engines (FwdArgs::engine) and their limits.
 constexpr int kEngineTc = 0, kEngineSync = 1, kEngineSmall = 2;
 int mixed_ctas_per_sm(int engine);    // CTAs per SM of a mixed-path engine

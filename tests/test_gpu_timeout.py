@@ -5,6 +5,7 @@ that nothing signals, before any copy or tensor-core operation is issued.  The w
 give up by itself, the call must report SUBMAT_ETIMEOUT with every row NaN, and the same
 plan must give its normal result once the flag is cleared.
 """
+import numpy as np
 import pytest
 
 import workloads as wl
@@ -25,7 +26,9 @@ def sm():
 @pytest.mark.parametrize("use_graph", [True, False])
 def test_wait_timeout_is_reported_and_the_plan_recovers(sm, use_graph):
     a = wl.overlap_uniform(n=1500)
-    plan = sm.submat_plan(a.rowptr, a.colind, 2, use_graph=use_graph)
+    # every row on the tcgen05 engine (the small engine, which has no pipeline waits, would
+    # take the rows of order <= 32 otherwise)
+    plan = sm.submat_plan(a.rowptr, a.colind, 2, use_graph=use_graph, small_max_m=0)
     v = torch.tensor(a.vals, device="cuda")
     out = torch.zeros_like(v)
     ref = sm.submat_invroot(plan, v, out, sync=True).clone()
@@ -40,3 +43,27 @@ def test_wait_timeout_is_reported_and_the_plan_recovers(sm, use_graph):
     plan.test_stall(False)
     y = sm.submat_invroot(plan, v, out, sync=True)
     assert torch.equal(y, ref)
+
+
+def test_wait_timeout_leaves_the_other_engines_rows(sm):
+    """With the default size buckets the rows of order <= 32 run on the small engine, which
+    the flag does not touch: they keep their values, the others are NaN."""
+    a = wl.overlap_uniform(n=1500)
+    m = a.row_sizes()
+    assert (m <= 32).any() and (m > 32).any()
+    plan = sm.submat_plan(a.rowptr, a.colind, 2)
+    v = torch.tensor(a.vals, device="cuda")
+    ref = sm.submat_invroot(plan, v, sync=True).cpu().numpy()
+    plan.test_stall(True)
+    out = torch.zeros_like(v)
+    with pytest.raises(sm.SubmatError) as ei:
+        sm.submat_invroot(plan, v, out, sync=True)
+    assert ei.value.name == "SUBMAT_ETIMEOUT"
+    plan.test_stall(False)
+    y = out.cpu().numpy()
+    for j in range(a.n):
+        seg = slice(a.rowptr[j], a.rowptr[j + 1])
+        if m[j] <= 32:
+            assert np.array_equal(y[seg], ref[seg])
+        else:
+            assert np.isnan(y[seg]).all()
