@@ -335,6 +335,7 @@ __device__ void vec_task(const VecTask& v) {
 // (mp).  All threads.
 constexpr float kTaylorStop = 0.05f;    // iterate until ||M - I||_F <= this (p >= 2)
 constexpr int kTaylorMaxDeg = 12;
+template <int RWY>       // rows per warp of the passes that serve y (loads in flight)
 __device__ void taylor_final(const VecTask& v, int Jy, int Ju, double* ay, float* au) {
   const int gt = threadIdx.x, gn = blockDim.x;
   double cj[kTaylorMaxDeg + 1];
@@ -358,7 +359,7 @@ __device__ void taylor_final(const VecTask& v, int Jy, int Ju, double* ay, float
           v.yl[i] = l;
         }
         __syncthreads();
-        matvec2_slices<2, 0, true>(v.q, v.plane, v.ld, v.e, v.yh, v.yl, v.my, au, v.t, v.m, v.mp);
+        matvec2_slices<RWY, 0, true>(v.q, v.plane, v.ld, v.e, v.yh, v.yl, v.my, au, v.t, v.m, v.mp);
         for (int i = gt; i < v.m; i += gn) ay[i] = cj[j] * v.y[i] + (ay[i] - v.my[i]);
       } else {
         matvec_slices_f32<3, 8, 0>(v.q, v.plane, v.ld, ldexpf(1.f, v.e - 7), au, v.t, v.m, v.mp);
@@ -416,7 +417,7 @@ __device__ float start_lo_slices(const __half* q, size_t plane, int ld, int e, i
   __syncthreads();
   float nb = 1.f;
   for (int t = 0; t < kStartLoSteps; ++t) {
-    matvec_slices_f32<2>(q, plane, ld, ldexpf(1.f, e - 7), a_s, b_s, m, mp);   // b = M_0 a
+    matvec_slices_f32<2, 8>(q, plane, ld, ldexpf(1.f, e - 7), a_s, b_s, m, mp);   // b = M_0 a
     float part = 0.f;
     for (int i = tid; i < m; i += blockDim.x) {
       const float d = a_s[i] - b_s[i];
@@ -1461,7 +1462,7 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
     // last step.  p >= 2: X_K M_K^(-1/p) is the limit (M_K = X_K^p M_0, all commuting), so
     // the carried column takes M_K^(-1/p) = (I - E)^(-1/p), E = I - M_K, as its Taylor
     // polynomial of degree J in E (Horner, one pass over M_K per degree), J chosen from
-    // ||E||_2 <= ||E||_F so that the tail is below 1e-10; this lets the iteration stop at
+    // ||E||_2 <= ||E||_F so that the tail is below 1e-9; this lets the iteration stop at
     // ||E||_F <= kTaylorStop instead of converging to the rounding floor (one GEMM iteration
     // fewer on average).  p = 1: Newton's X (2I - M) as a product, then FP64 refinement.
     double resid = 1e300;
@@ -1483,7 +1484,9 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
         while (J < kTaylorMaxDeg && !(powf(eps, (float)(J + 1)) <= target * (1.f - eps))) ++J;
         return J;
       };
-      taylor_final(vec_of(B3[mi], 0.0, 0.0, true), degree(1e-10f), degree(1e-6f), ayg, aug);
+      // y's tail far below the 1e-6 target; u only feeds the 1e-3 residual test
+      taylor_final<SMALL ? 2 : 4>(vec_of(B3[mi], 0.0, 0.0, true), degree(1e-9f), degree(1e-5f),
+                                  ayg, aug);
       // column pos of the result (lambda_bar^(-1/p) X e_pos, or lambda_bar^(1/p) X^(p-1)
       // M_0 e_pos for A^(1/p)) and the residual F^p s_pos - e_pos = u - e_pos of
       // F = lambda_bar^(-1/p) X
