@@ -520,6 +520,7 @@ def main():
     log("plan")
     plan = sm.submat_plan(a.rowptr, a.colind, p, precision=args.precision, shard=(rank, world))
     row_b, row_e = sm.shard_rows(a.rowptr, world, rank)
+    launches_per_step = plan.engine_launches()
     log("warm-up")
     vals = torch.tensor(a.vals, device=dev)
     out = torch.empty_like(vals)
@@ -668,7 +669,7 @@ def main():
         "e2e": {"value": rows_total / (e2e_step / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(a.nnz * 8 * world),
                 "d2h_bytes_per_step": int(a.nnz * 8 * world)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
     if fp64 is not None:

@@ -168,6 +168,7 @@ class Plan:
             on_dev = 0
             rp_ptr, ci_ptr = rp.ctypes.data, ci.ctypes.data
             n, nnz = rp.shape[0] - 1, ci.shape[0]
+        self.rowptr_host = (rp.cpu().numpy() if isinstance(rp, torch.Tensor) else rp).astype(np.int32)
         csr = CSR(n, nnz, rp_ptr, ci_ptr if nnz > 0 else None, on_dev)
         o = Opts()
         lib.submat_default_opts(ctypes.byref(o))
@@ -194,6 +195,9 @@ class Plan:
         self.p = int(p)
         self.precision = precision
         self.root_sign = int(root_sign)
+        self.small_max_m = int(o.small_max_m)
+        self.sync_max_m = int(o.sync_max_m)
+        self.shard = (int(shard[0]), int(shard[1]))
         self.device = torch.device("cuda", torch.cuda.current_device())
         self._fwd_gen = 0              # forwards run on this plan (the backward's input)
 
@@ -209,6 +213,21 @@ class Plan:
         pos = np.zeros(self.n, dtype=np.int32)
         _check(self._lib, self._lib.submat_plan_rows(self._h, m.ctypes.data, pos.ctypes.data))
         return m, pos
+
+    def engine_launches(self):
+        """Kernel launches of one forward: one per engine that gets rows (the plan's size
+        buckets; the FP64 path has one), plus the fallback kernel."""
+        if self.precision == "fp64":
+            return 2
+        m, _ = self.rows()
+        b, e = shard_rows(self.rowptr_host, self.shard[1], self.shard[0])
+        m = m[b:e]
+        if self.precision == "mixed_sync":
+            return 1 + int(len(m) > 0)
+        small = m <= self.small_max_m
+        sync = (~small) & (m <= self.sync_max_m)
+        tc = ~(small | sync)
+        return 1 + int(small.any()) + int(sync.any()) + int(tc.any())
 
     def test_stall(self, on: bool):
         """``submat_test_stall``: make the tensor-core forward's first pipeline wait run out
