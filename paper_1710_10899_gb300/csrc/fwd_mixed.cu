@@ -41,8 +41,9 @@
 //              3-stage mbarrier pipeline.  A full-width tile issues the fifteen plane
 //              products of a k-step as eight MMAs over B's concatenated planes (N up to
 //              240), and the affine term alpha Y (Y = B) enters the accumulators through
-//              MMAs with an exact identity operand -alpha' I on the k-steps of the tile's
-//              diagonal block, so the epilogue reads no Y.  Roles: warps 0-7 run the epilogue (two per TMEM
+//              the level-0 A plane: on the k-steps of the tile's diagonal block the MMA
+//              warp subtracts the exact integer alpha' from its diagonal entries in the
+//              stage, so A_0 B_t adds -alpha' B_t to level t and the epilogue reads no Y.  Roles: warps 0-7 run the epilogue (two per TMEM
 //              lane quarter), warp 8 issues TMA, warp 9 issues MMAs, warps 10-11 apply the
 //              iteration's step to the carried column (384 threads).
 //              All working matrices are symmetric, so a row-major B read as K-major
@@ -76,7 +77,8 @@ constexpr int kPlanesPerCta = 35;  // 6 matrices x 5 planes, 4 planes of room fo
 // Every product of the iteration has the form C = c (alpha Y - A Y), i.e. the step matrix
 // T = c (alpha I - A) applied to Y, with A = M_k and Y the B operand (all matrices are
 // symmetric polynomials in S, so they commute).  The tcgen05 engine adds -alpha Y to the
-// accumulators with MMAs; the mma.sync engine reads Y's entry at the output position.  Flags:
+// accumulators through its level-0 A plane; the mma.sync engine reads Y's entry at the
+// output position.  Flags:
 // accumulate ||C - I||_F^2 over the leading m x m block, and/or max |C|.
 enum EpiFlag { EPI_NORM = 1, EPI_AMAX = 2 };
 
@@ -469,11 +471,6 @@ constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 107520 B
 constexpr int TC_CH = TC_N / 8;                        // 8-column chunks per tile row (12)
 constexpr int TC_SROW = 4 * TC_CH + 1;                 // units per staged row (49)
 constexpr int TC_STAGING_BYTES = TC_M * TC_SROW * 16;  // 100352 B
-// Identity operand of the affine term (see gemm_tc): a K-major 240 x 16 FP16 tile whose only
-// nonzeros, -alpha', sit at (112 + k, k); rows [112 - o, 240 - o) of it are the 128 x 16
-// slice of -alpha' I for a k-step o = 16 kt - 128 tm columns into the tile's diagonal block.
-constexpr int TC_Z_ROWS = TC_M + TC_M - TC_K;          // 240
-constexpr int TC_Z_BYTES = TC_Z_ROWS * TC_K * 2;       // 7680 B (1024-aligned in the layout)
 constexpr float kAlphaQuantum = 1.f / 64.f;            // alpha' = alpha 2^(7 - e) is an integer
 constexpr int TC_BUF_COLS = NSL * TC_N;                // 480 TMEM columns
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;           // polls before a wait gives up
@@ -499,7 +496,6 @@ struct TcState {            // pipeline counters; each role keeps its own copy
 struct TcCtx {
   unsigned char* stages;    // 1024-aligned shared memory
   uint4* staging;           // [TC_M][TC_SROW] units of the tile being drained
-  __half* z;                // identity operand (TC_Z_BYTES, 1024-aligned)
   uint64_t* full;           // [TC_STAGES]
   uint64_t* empty;          // [TC_STAGES]
   uint64_t* tmem_full;      // accumulators ready
@@ -602,21 +598,6 @@ __device__ __forceinline__ void mma_kstep_narrow(uint32_t d0, uint64_t da0, uint
     }
   }
 }
-// The affine term: -alpha' I (one exact FP16 plane, level 0) times B's five planes, added to
-// levels 0..4.  Full tiles: two MMAs with N = 240 over the concatenated planes.
-__device__ __forceinline__ void mma_identity_full(uint32_t d0, uint64_t dz, uint64_t db0) {
-  constexpr uint32_t i240 = tc::idesc_f16(TC_M, 240);
-  constexpr uint64_t RB = (TC_K * 2) >> 4;
-  tc::mma_f16(d0 + 0, dz, db0, i240, 1u);
-  tc::mma_f16(d0 + 240, dz, db0 + 240 * RB, i240, 1u);
-}
-__device__ __forceinline__ void mma_identity_narrow(uint32_t d0, uint64_t dz, uint64_t db0,
-                                                    uint32_t idesc) {
-#pragma unroll
-  for (int t = 0; t < NSL; ++t)
-    tc::mma_f16(d0 + t * TC_N, dz, db0 + (uint64_t)((t * TC_B_PLANE) >> 4), idesc, 1u);
-}
-
 // C = A B^T on the tcgen05 engine (see the header comment).  All TC_THREADS threads call it.
 // The GEMMs of one iteration run back to back with the GEMM warps' barrier between them;
 // full_in / full_out make the first one start and the last one end with a whole-block
@@ -672,12 +653,8 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
     }
   } else if (warp == TC_MMA_WARP) {
     if (lane == 0) {                                   // ---- MMA issuer
-      // -alpha' on the identity operand's band (the previous GEMM's MMAs have completed:
-      // its epilogue drained every tile before the barrier that started this GEMM)
+      // -alpha' = -alpha 2^(7 - e_A), an integer below 2^11 (alpha is a multiple of 1/64)
       const __half nz = __float2half_rn(-ldexpf(io.alpha, 7 - A.e));
-      for (int k = 0; k < TC_K; ++k) c.z[sw32_index(TC_M - TC_K + k, k)] = nz;
-      tc::fence_proxy_async_shared();
-      const uint64_t dz0 = tc::desc_sw32(tc::saddr(c.z));
       for (int t = 0; t < ntiles && !*c.abort_s; ++t) {
         int tm, tn;
         tc_tile(t, ntn, tm, tn);
@@ -707,6 +684,20 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
           // operand descriptors of the stage; every offset added below is a compile-time
           // constant added to the 14-bit start-address field (no carry: shared addresses
           // stay below 2^18 bytes)
+          if (kt >= kd0 && kt < kd1) {
+            // the affine term: A_0 - alpha' I on this k-step's 16 diagonal entries of the
+            // stage's level-0 A plane (integers below 2^11 stay exact in FP16), so the
+            // products A_0 B_t add -alpha' B_t to level t; then hand the plane back to the
+            // tensor core's proxy
+            __half* a0 = reinterpret_cast<__half*>(c.stages + s * TC_STAGE_BYTES);
+            const int o = (kt - kd0) * TC_K;
+#pragma unroll
+            for (int k = 0; k < TC_K; ++k) {
+              const int idx = sw32_index(o + k, k);
+              a0[idx] = __hadd(a0[idx], nz);
+            }
+            tc::fence_proxy_async_shared();
+          }
           const uint32_t sa = tc::saddr(c.stages + s * TC_STAGE_BYTES);
           const uint64_t da0 = tc::desc_sw32(sa);
           const uint64_t db0 = tc::desc_sw32(sa + NSL * TC_A_PLANE);
@@ -715,13 +706,6 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
             mma_kstep_full(d0, da0, db0, acc0);
           else
             mma_kstep_narrow(d0, da0, db0, idesc, acc0);
-          if (kt >= kd0 && kt < kd1) {
-            const uint64_t dz = dz0 + (uint64_t)(((TC_M - TC_K) - (kt - kd0) * TC_K) * TC_K * 2 >> 4);
-            if (full)
-              mma_identity_full(d0, dz, db0);
-            else
-              mma_identity_narrow(d0, dz, db0, idesc);
-          }
           tc::mma_commit(&c.empty[s]);                 // frees the stage when these MMAs finish
           ++st.cit;
         }
@@ -1158,11 +1142,11 @@ constexpr size_t kSmallVecBytes =
     ((3 * kSmallVmax + kRedDoubles) * sizeof(double) + kSmallVmax * sizeof(int32_t) + 1023) /
     1024 * 1024;
 constexpr size_t kSmallPlaneBytes = (size_t)kSmallLD * kSmallLD * sizeof(__half);
-// shared memory before the barrier tail: tcgen05: TMA stages + the epilogue's staging area +
-// the identity operand; mma.sync: its cp.async stages; small: vectors + resident planes
+// shared memory before the barrier tail: tcgen05: TMA stages + the epilogue's staging area;
+// mma.sync: its cp.async stages; small: vectors + resident planes
 template <int ENG>
 __host__ __device__ constexpr size_t stage_area() {
-  return ENG == ENG_TC ? (size_t)TC_STAGE_AREA + TC_STAGING_BYTES + TC_Z_BYTES
+  return ENG == ENG_TC ? (size_t)TC_STAGE_AREA + TC_STAGING_BYTES
          : ENG == ENG_SYNC ? (size_t)SY_STAGE_AREA
                            : kSmallVecBytes + kSmallPlanes * kSmallPlaneBytes;
 }
@@ -1170,6 +1154,10 @@ __host__ __device__ constexpr size_t stage_area() {
 constexpr size_t kVecBytes = 4 * SUBMAT_MAX_M * sizeof(double) + kRedDoubles * sizeof(double) +
                              SUBMAT_MAX_M * sizeof(int32_t);
 static_assert(kVecBytes <= (size_t)SY_STAGE_AREA, "vector area must fit in the stage area");
+// the Taylor finish's vectors follow it (3 doubles and 5 floats per entry)
+static_assert(kVecBytes + 44 * (size_t)SUBMAT_MAX_M <= (size_t)SY_STAGE_AREA &&
+                  kVecBytes + 44 * (size_t)SUBMAT_MAX_M <= (size_t)TC_STAGE_AREA + TC_STAGING_BYTES,
+              "finish vectors must fit in the idle stage area");
 
 template <int ENG>
 __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
@@ -1223,10 +1211,6 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
     tcx.tmem_full = bars + 2 * TC_STAGES;
     tcx.tmem_empty = bars + 2 * TC_STAGES + 1;
     tcx.staging = reinterpret_cast<uint4*>(sm + TC_STAGE_AREA);
-    tcx.z = reinterpret_cast<__half*>(sm + TC_STAGE_AREA + TC_STAGING_BYTES);
-    for (int i = tid; i < TC_Z_BYTES / 16; i += blockDim.x)
-      reinterpret_cast<uint4*>(tcx.z)[i] = make_uint4(0u, 0u, 0u, 0u);
-    __syncthreads();
     tcx.abort_s = abort_s;
     tcx.tmem = *tmem_holder;
     tcx.tm_a = &a.tm_a;
@@ -1470,12 +1454,28 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
     const double c = pow(lam, -1.0 / (double)p);               // F = c X
     if (!bad && track) {
       const double c_out = a.sign < 0 ? c : pow(lam, 1.0 / (double)p);
+      // the finish's vectors: in shared memory (the GEMMs' stage and staging areas are idle
+      // now), y, its Horner accumulator and M y as doubles, then u, y's double-float split,
+      // M u and u's accumulator as floats; the small engine keeps its shared vector plane
+      double *yf = yg, *ayf = ayg, *myf = myg;
+      float *uf = ug, *yhf = yhg, *ylf = ylg, *tf = tg, *auf = aug;
+      if (!SMALL) {
+        yf = reinterpret_cast<double*>(sm + kVecBytes);
+        ayf = yf + mp;
+        myf = ayf + mp;
+        uf = reinterpret_cast<float*>(myf + mp);
+        yhf = uf + mp;
+        ylf = yhf + mp;
+        tf = ylf + mp;
+        auf = tf + mp;
+        for (int i = tid; i < mp; i += blockDim.x) yf[i] = yg[i];
+      }
       // residual vector u = M_K e_pos (row pos of the symmetric M_K = X_K^p M_0, up to the
       // products' rounding), carried through the last step with y
       for (int i = tid; i < mp; i += blockDim.x) {
         float h = 0.f, l = 0.f;
         if (i < m) load1_df(B3[mi].q, plane, (size_t)pos * LD + i, B3[mi].e, h, l);
-        ug[i] = h + l;
+        uf[i] = h + l;
       }
       __syncthreads();
       const float eps = sqrtf(nrm2);
@@ -1485,15 +1485,16 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
         return J;
       };
       // y's tail far below the 1e-6 target; u only feeds the 1e-3 residual test
-      taylor_final<SMALL ? 2 : 4>(vec_of(B3[mi], 0.0, 0.0, true), degree(1e-9f), degree(1e-5f),
-                                  ayg, aug);
+      const VecTask vf{B3[mi].q, plane, LD, B3[mi].e, m, mp, p, ny, 0.0, 0.0,
+                       yf, uf, yhf, ylf, myf, tf, true};
+      taylor_final<SMALL ? 2 : 4>(vf, degree(1e-9f), degree(1e-5f), ayf, auf);
       // column pos of the result (lambda_bar^(-1/p) X e_pos, or lambda_bar^(1/p) X^(p-1)
       // M_0 e_pos for A^(1/p)) and the residual F^p s_pos - e_pos = u - e_pos of
       // F = lambda_bar^(-1/p) X
       float r = 0.f;
       for (int i = tid; i < m; i += blockDim.x) {
-        y_s[i] = c_out * yg[i];
-        const float d = ug[i] - (i == pos ? 1.f : 0.f);
+        y_s[i] = c_out * yf[i];
+        const float d = uf[i] - (i == pos ? 1.f : 0.f);
         r += d * d;
       }
       r = warp_sum_f(r);
