@@ -16,7 +16,7 @@ The line carries, besides the contract's keys:
   * ``roofline``: the method's flops (sum over rows of k_j (p+1) 2 m_j^3, executed iteration
     counts, true orders) per launch of the dominant kernel over its CUDA-event time, against
     the measured dense BF16 (= FP16) rate; the tensor-core work the engine executes for them
-    (15 FP16 slice products per product) is reported beside it as
+    (15 FP16 slice products per product, 10 in GEMMs without level 4) is reported beside it as
     ``executed_tensor_tflops``;
   * ``fp64_path``: the all-FP64 GPU path on the same input (median of --fp64-steps steps)
     and its error against the oracle on every row;
@@ -338,7 +338,8 @@ def roofline_mixed(reps, pk, pk_kind):
             "work": "sum over rows of k_j (p+1) 2 m_j^3 (executed iterations, true orders)",
             "executed_tensor_tflops": executed / (kern_ms / 1e3) / 1e12,
             "executed_tensor_frac": executed / (kern_ms / 1e3) / 1e12 / peak,
-            "executed_work": "15 FP16 slice products x 2 m_j^3 per executed GEMM"}
+            "executed_work": "FP16 slice products (15, or 10 without level 4) x 2 m_j^3 per "
+                             "executed GEMM"}
 
 
 def roofline_fp64(reps):

@@ -136,10 +136,19 @@ typedef struct {
                               the tuned default.  The rows are ordered by decreasing m, so
                               each engine gets one contiguous run of the work queue and one
                               persistent launch                                           */
+  double level4_lo;        /* SUBMAT_PREC_MIXED_F16, tcgen05 engine: an iteration whose
+                              spectral interval [lo_k, 1] has lo_k >= level4_lo takes its
+                              GEMMs without the five level-4 slice products (s + t = 4, the
+                              terms of relative size ~2^-32; ten FP16 products per GEMM
+                              instead of fifteen, and plane 4 is not loaded); 0 drops them in
+                              every iteration, values above 1 in none; < 0 selects the
+                              default (SUBMAT_LEVEL4_LO)                                   */
 } submat_opts;
 
 /* Largest order the small-submatrix engine takes. */
 #define SUBMAT_SMALL_MAX_M 32
+/* Default of submat_opts.level4_lo. */
+#define SUBMAT_LEVEL4_LO 2.0
 
 typedef struct {
   int64_t n_rows;          /* submatrices processed by the last forward                  */
@@ -151,9 +160,9 @@ typedef struct {
   double max_resid;        /* largest FP64 column residual seen before the fallback      */
   double sum_m3;           /* sum over rows of m^3 (true sizes)                           */
   double flops_tensor;     /* tensor-core flops executed by the last forward: sum over
-                              rows of (GEMMs executed) * 15 FP16 slice products *
-                              2 m_j^3 (true m_j; p GEMMs per iteration for p >= 2;
-                              two for p = 1, plus its final X product)                   */
+                              GEMMs executed of (FP16 slice products: 15, or 10 without
+                              level 4) * 2 m_j^3 (true m_j; p GEMMs per iteration for
+                              p >= 2; two for p = 1, plus its final X product)           */
   double flops_fp64;       /* FP64 flops of the last forward (FP64 path: iterations;
                               mixed path: column refinement; both: fallback)             */
   float ms_kernel;         /* device time of the last forward's main (Newton) kernel,

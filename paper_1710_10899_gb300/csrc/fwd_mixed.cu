@@ -94,6 +94,7 @@ struct GemmIO {     // what every GEMM call shares within one submatrix
   float* norm_part;  // ||.||_F^2 partial sums, one slot per writing warp (summed in order)
   unsigned* amax_s;
   float c, alpha;          // C = c (alpha Y - A B)
+  int lmax;                // tcgen05 engine: highest slice level L = s + t multiplied (3 or 4)
 };
 
 // Exponent for values bounded by b (with a relative margin for rounding).
@@ -586,10 +587,30 @@ __device__ __forceinline__ void mma_kstep_full(uint32_t d0, uint64_t da0, uint64
   tc::mma_f16(d0 + 288, da0 + 3 * PA, db0, i192, 1u);
   tc::mma_f16(d0 + 384, da0 + 4 * PA, db0, i96, 1u);
 }
+// Levels 0..3 only (A_s B_t with s + t <= 3, planes 0..3): ten products as six MMAs
+// (N = 192, 192, 144, 144, 192, 96) into TMEM columns 0..383; level 4's columns are not
+// written and not read.
+__device__ __forceinline__ void mma_kstep_full_l3(uint32_t d0, uint64_t da0, uint64_t db0,
+                                                  uint32_t acc0) {
+  constexpr uint32_t i192 = tc::idesc_f16(TC_M, 192), i144 = tc::idesc_f16(TC_M, 144),
+                     i96 = tc::idesc_f16(TC_M, 96);
+  constexpr uint64_t PA = TC_A_PLANE >> 4, RB = (TC_K * 2) >> 4;   // 16-byte units
+  // s = 0: B rows 0..383 -> columns 0..383 (overwrite at the first k-step)
+  tc::mma_f16(d0 + 0, da0, db0 + 0 * RB, i192, acc0);
+  tc::mma_f16(d0 + 192, da0, db0 + 192 * RB, i192, acc0);
+  // s = 1: B rows 0..287 -> columns 96..383
+  tc::mma_f16(d0 + 96, da0 + PA, db0 + 0 * RB, i144, 1u);
+  tc::mma_f16(d0 + 240, da0 + PA, db0 + 144 * RB, i144, 1u);
+  // s = 2: B rows 0..191 -> columns 192..383; s = 3: B rows 0..95 -> columns 288..383
+  tc::mma_f16(d0 + 192, da0 + 2 * PA, db0, i192, 1u);
+  tc::mma_f16(d0 + 288, da0 + 3 * PA, db0, i96, 1u);
+}
+// Levels 0..LMAX as separate products of width N = nw.
+template <int LMAX>
 __device__ __forceinline__ void mma_kstep_narrow(uint32_t d0, uint64_t da0, uint64_t db0,
                                                  uint32_t idesc, uint32_t acc0) {
 #pragma unroll
-  for (int L = 0; L < NSL; ++L) {
+  for (int L = 0; L <= LMAX; ++L) {
 #pragma unroll
     for (int sa_i = 0; sa_i <= L; ++sa_i) {
       const uint64_t da = da0 + (uint64_t)((sa_i * TC_A_PLANE) >> 4);
@@ -611,6 +632,8 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
   const int mp = io.mp;
   const int ntm = (mp + TC_M - 1) / TC_M, ntn = (mp + TC_N - 1) / TC_N, KT = mp / TC_K;
   const int ntiles = tc_ntiles(ntm, ntn);
+  const bool l4 = io.lmax >= 4;                      // level 4 multiplied (all five planes)
+  const int np = l4 ? NSL : NSL - 1;
   // generic-proxy writes (planes, shared vectors) before async-proxy reads/writes
   tc::fence_proxy_async_global();
   tc::fence_proxy_async_shared();
@@ -638,13 +661,12 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
           }
           unsigned char* sa = c.stages + s * TC_STAGE_BYTES;
           unsigned char* sb = sa + NSL * TC_A_PLANE;
-          tc::mbar_arrive_expect_tx(&c.full[s], TC_STAGE_BYTES);
-#pragma unroll
-          for (int q = 0; q < NSL; ++q)
+          // planes 0..lmax of both operands (levels up to lmax use no others)
+          tc::mbar_arrive_expect_tx(&c.full[s], np * (TC_A_PLANE + TC_B_PLANE));
+          for (int q = 0; q < np; ++q)
             tc::tma_load_3d(sa + q * TC_A_PLANE, c.tm_a, kt * TC_K, tm * TC_M, A.plane0 + q,
                             &c.full[s]);
-#pragma unroll
-          for (int q = 0; q < NSL; ++q)
+          for (int q = 0; q < np; ++q)
             tc::tma_load_3d(sb + q * TC_B_PLANE, c.tm_b, kt * TC_K, tn * TC_N, B.plane0 + q,
                             &c.full[s]);
           ++st.pit;
@@ -702,10 +724,14 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
           const uint64_t da0 = tc::desc_sw32(sa);
           const uint64_t db0 = tc::desc_sw32(sa + NSL * TC_A_PLANE);
           const uint32_t acc0 = kt != 0;               // the first k-step overwrites
-          if (full)
+          if (full && l4)
             mma_kstep_full(d0, da0, db0, acc0);
+          else if (full)
+            mma_kstep_full_l3(d0, da0, db0, acc0);
+          else if (l4)
+            mma_kstep_narrow<NSL - 1>(d0, da0, db0, idesc, acc0);
           else
-            mma_kstep_narrow(d0, da0, db0, idesc, acc0);
+            mma_kstep_narrow<NSL - 2>(d0, da0, db0, idesc, acc0);
           tc::mma_commit(&c.empty[s]);                 // frees the stage when these MMAs finish
           ++st.cit;
         }
@@ -721,7 +747,7 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
     const int q4 = warp & 3, half = warp >> 2;
     const int etid = tid;                              // 0 .. 255 (warps 0..7)
     // the level sums count in units of cscale = 2^(A.e + B.e - 14) and already hold
-    // A B - alpha Y (the identity operand's MMAs), so C = -c cscale w
+    // A B - alpha Y (alpha' sits on the level-0 A plane's diagonal), so C = -c cscale w
     const float c_s = -ldexpf(io.c, A.e + B.e - 14);
     float nrm = 0.f, amax = 0.f;
     const int rt = q4 * 32 + lane;                    // phase 1: this thread's tile row
@@ -752,7 +778,13 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
         for (int c0 = cb; c0 < ce; c0 += 8) {          // warp-uniform bounds
           float acc[NSL][8];
 #pragma unroll
-          for (int L = 0; L < NSL; ++L) tc::tmem_ld8(tbase + L * TC_N + c0, acc[L]);
+          for (int L = 0; L < NSL - 1; ++L) tc::tmem_ld8(tbase + L * TC_N + c0, acc[L]);
+          if (l4) {
+            tc::tmem_ld8(tbase + (NSL - 1) * TC_N + c0, acc[NSL - 1]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[NSL - 1][k] = 0.f;
+          }
           tc::tmem_ld_wait();
 #pragma unroll
           for (int k2 = 0; k2 < 4; ++k2) {
@@ -1340,7 +1372,7 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
     __threadfence();             // planes are read next through L2 (cp.async.cg / TMA)
     __syncthreads();
 
-    GemmIO io{mp, m, p, LD, plane, norm_part, amax_s, 0.f, 0.f};
+    GemmIO io{mp, m, p, LD, plane, norm_part, amax_s, 0.f, 0.f, 4};
     // vt: vector work to run with this GEMM (tcgen05: on the vector warps during this and
     // the iteration's later GEMMs; mma.sync: before the GEMM on all warps).  first / last:
     // the GEMM starts / ends an iteration's sequence (see gemm_tc).
@@ -1360,7 +1392,7 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
     };
 
     int xc = 0, mi = 0;
-    int n_gemm = 0;
+    int n_prod = 0;            // FP16 slice products executed (15 or 10 per GEMM)
     const float tol2 = (float)(a.tol * a.tol * (double)m);
     const float stag2 = 1e-4f * (float)m;       // (1e-2)^2 m
     int iters = 0;
@@ -1374,9 +1406,13 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
     while (!bad) {
       // p >= 2: close enough to I for the final Taylor step (see below)
       if (track && nrm2 <= kTaylorStop * kTaylorStop) break;
-      const ScaledStep st = scaled_step(fmaxf(lo, 1.f - sqrtf(nrm2)), p, kAlphaQuantum);
+      const float lo_k = fmaxf(lo, 1.f - sqrtf(nrm2));
+      const ScaledStep st = scaled_step(lo_k, p, kAlphaQuantum);
       io.c = st.c;
       io.alpha = st.alpha;
+      // tcgen05 engine: without the level-4 products once lo_k is high enough (a product's
+      // error enters the limit X_K M_K^(-1/p) scaled by about 1 / (p lambda_min(M_{k+1})))
+      io.lmax = (TC && lo_k >= a.level4_lo) ? 3 : 4;
       const Mat Mk = B3[mi];
       const VecTask vt = vec_of(Mk, (double)st.c, (double)st.alpha, false);
       if (track) {
@@ -1408,7 +1444,7 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
         if (tid == 0) *amax_s = 0u;
         __syncthreads();
         if (!gemm(Mk, X[xc], X[xc ^ 1], X[xc], EPI_AMAX, nullptr)) { stop = true; break; }
-        ++n_gemm;
+        n_prod += io.lmax >= 4 ? 15 : 10;
         xmax = __uint_as_float(*amax_s);
         xc ^= 1;
       }
@@ -1422,7 +1458,7 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
           stop = true;
           break;
         }
-        ++n_gemm;
+        n_prod += io.lmax >= 4 ? 15 : 10;
         src = dst;
         dst = 3 - mi - dst;                     // the buffer that is neither M_k nor P_s
       }
@@ -1515,7 +1551,7 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
         pending = j;
         break;
       }
-      ++n_gemm;
+      n_prod += io.lmax >= 4 ? 15 : 10;
       xc ^= 1;
       SliceLoad xl{X[xc].q, plane, LD, ldexp(1.0, X[xc].e - 7)};
       const float xs = ldexpf(1.f, X[xc].e - 7);
@@ -1545,7 +1581,7 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
       atomic_max_nonneg(&a.ctr->resid_max_bits, resid);
       atomicAdd(&a.ctr->flops_fp64, refine_flops(m, p, a.refine_steps));
       // fifteen FP16 slice products per GEMM, counted with the true order m
-      atomicAdd(&a.ctr->flops_tensor, (double)n_gemm * 15.0 * 2.0 * (double)m * m * m);
+      atomicAdd(&a.ctr->flops_tensor, (double)n_prod * 2.0 * (double)m * m * m);
       // the method's own count: (p+1) dense products of order m per iteration (+ p = 1's
       // final X product), whatever this engine executes for them
       atomicAdd(&a.ctr->flops_alg,
