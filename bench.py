@@ -21,8 +21,10 @@ The line carries, besides the contract's keys:
   * ``fp64_path``: the all-FP64 GPU path on the same input (median of --fp64-steps steps)
     and its error against the oracle on every row;
   * ``extras``: the other workloads (p = 1 and 3, the positive root, the small FP64
-    workload, the clustered and the block-sparse workloads, the adjoint), each timed and
-    checked against the oracle (every row, or a seeded sample stratified by row size).
+    workload, the clustered and the block-sparse workloads, the adjoint with its atomic and
+    deterministic scatters), each timed and checked against the oracle (every row, or a
+    seeded sample stratified by row size), and the CG solves of Sec. 4.4 on the stand-ins
+    for its matrices, plain and preconditioned with the method's result.
 
 With N > 1 (torchrun) the workload is built N times larger (same recipe, n x N rows) and
 its rows are sharded across ranks (Sec. 6.1.1: every rank holds the whole matrix and
@@ -65,7 +67,11 @@ EXTRAS = [
     ("clustered", "overlap_clustered", 2, "mixed", -1, 512, 1, 3),
     ("block", "block_overlap", 2, "mixed", -1, 128, 1, 1),
     ("backward", "overlap_grad", 2, "mixed", -1, 0, 1, 3),
+    ("cg", "cg_standins", 2, "mixed", -1, 0, 1, 3),
 ]
+CG_STANDINS = (("laplace2d_aniso(nx=64,eps=0.01)", "laplace2d_aniso", {}),
+               ("jump3d(nx=16,contrast=1e4)", "jump3d", {}),
+               ("overlap_uniform(n=4096,kappa=1e5)", "overlap_uniform", {"n": 4096, "kappa": 1e5}))
 
 
 def parse():
@@ -391,25 +397,24 @@ def backward_block(sm, plan, a, vals, flush, steps, warm, clocks_mhz):
     import torch
     import workloads as wl
     w = torch.tensor(wl.random_on_pattern(a, seed=1), device="cuda")
-    stream = torch.cuda.current_stream()
     sm.submat_invroot(plan, vals)
-    for _ in range(warm):
-        sm.submat_invroot_backward(plan, w)
-    torch.cuda.synchronize()
-    ms = []
-    g = None
-    for _ in range(steps):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        g = sm.submat_invroot_backward(plan, w)
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
+    ms, g = time_backward(sm, plan, w, flush, steps, warm)
     med = statistics.median(ms)
     gref = _PRE["grad_ref"]
     gh = g.cpu().numpy()
+    # the deterministic (atomic-free) scatter: per-row gradients in waves, summed per entry
+    # in a fixed order
+    pdet = sm.submat_plan(a.rowptr, a.colind, 2, grad_deterministic=True)
+    sm.submat_invroot(pdet, vals)
+    ms_det, g_det = time_backward(sm, pdet, w, flush, steps, warm)
+    g_det2 = sm.submat_invroot_backward(pdet, w)
+    gd = g_det.cpu().numpy()
+    det = {"ms_per_call_median": statistics.median(ms_det),
+           "value": a.n / (statistics.median(ms_det) / 1e3), "unit": UNIT,
+           "grad_rel_err_vs_oracle": float(np.linalg.norm(gd - gref) / np.linalg.norm(gref)),
+           "bitwise_repeatable": bool(torch.equal(g_det, g_det2)),
+           "max_abs_diff_vs_atomic_rel_to_max": float(np.abs(gd - gh).max() / np.abs(gh).max())}
+    del pdet
     m = a.row_sizes().astype(np.float64)
     work = float((16.0 * m ** 3).sum())
     mhz = clocks_mhz or 2070.0
@@ -425,7 +430,76 @@ def backward_block(sm, plan, a, vals, flush, steps, warm, clocks_mhz):
                      "peak_kind": f"FP32 FMA rate at {mhz:.0f} MHz (152 SMs x 128 lanes x 2)",
                      "work": "16 m_j^3 per row (Jacobi sweeps and eigenvector products "
                              "counted as FP64-equivalent flops, executed in double-float "
-                             "FP32 arithmetic)"}}}
+                             "FP32 arithmetic)"},
+        "deterministic": det}}
+
+
+def time_backward(sm, plan, w, flush, steps, warm):
+    """``warm`` untimed and ``steps`` CUDA-event timed backward calls (L2 flushed before
+    each, not timed).  Returns (per-call ms, last gradient)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        sm.submat_invroot_backward(plan, w)
+    torch.cuda.synchronize()
+    ms, g = [], None
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g = sm.submat_invroot_backward(plan, w)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms, g
+
+
+def cg_block(sm, spec, flush):
+    """The preconditioning application (Sec. 4.4) on the stand-ins for the section's
+    matrices: CG on A x = ones (threshold 1e-6), plain and with K = the p = 2 result of the
+    method (K ~ A^(-1/2)); per matrix the steps, the CUDA-event time of a solve (median of
+    ``steps`` after ``warm`` untimed ones; the solver's host loop reads two scalars per step)
+    and of the forward that makes K."""
+    import torch
+    _, _, p, prec, _, _, warm, steps = spec
+    import workloads as wl
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ms, res = [], None
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms), res
+
+    for label, fname, kw in CG_STANDINS:
+        a = wl.WORKLOADS[fname](**kw) if fname in wl.WORKLOADS else getattr(wl, fname)(**kw)
+        plan = sm.submat_plan(a.rowptr, a.colind, p, precision=prec)
+        v = torch.tensor(a.vals, device="cuda")
+        k = torch.empty_like(v)
+        ms_fwd, _ = timed(lambda: sm.submat_invroot(plan, v, k))
+        ms_plain, (_, it_plain, rel_plain) = timed(lambda: sm.submat_pcg(plan, v))
+        ms_k, (_, it_k, rel_k) = timed(lambda: sm.submat_pcg(plan, v, vals_k=k))
+        out[label] = {"n": a.n, "nnz": a.nnz, "steps_plain": it_plain, "steps_k": it_k,
+                      "rel_resid_plain": rel_plain, "rel_resid_k": rel_k,
+                      "ms_solve_plain": ms_plain, "ms_solve_k": ms_k,
+                      "ms_per_step_plain": ms_plain / max(1, it_plain),
+                      "ms_per_step_k": ms_k / max(1, it_k),
+                      "ms_forward_k": ms_fwd, "k_precision": prec}
+        del plan
+    return {"workload": "CG stand-ins for Sec. 4.4 (b = ones, threshold 1e-6)",
+            "steps": steps, "warmup": warm, "solves": out}
 
 
 _PRE = {}
@@ -487,6 +561,9 @@ def main():
     import workloads as wl
     for spec in extras:
         name, wname, ep, prec, sign, nrows, _, _ = spec
+        if name == "cg":                          # CG solves: no forward oracle needed
+            extra_inputs[name] = (None, None, None)
+            continue
         key = (wname, args.n if wname == args.workload else 0)
         if wname == args.workload:
             ea = a
@@ -647,7 +724,10 @@ def main():
             ea, ref, rows = extra_inputs[name]
             log(f"extra: {name}")
             try:
-                extra_out[name] = run_extra(sm, spec, ea, ref, rows, flush, pk, pk_kind, mhz)
+                if name == "cg":
+                    extra_out[name] = cg_block(sm, spec, flush)
+                else:
+                    extra_out[name] = run_extra(sm, spec, ea, ref, rows, flush, pk, pk_kind, mhz)
             except Exception as e:                  # report, keep the main line
                 extra_out[name] = {"error": f"{type(e).__name__}: {e}"}
             torch.cuda.empty_cache()
