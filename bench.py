@@ -16,7 +16,7 @@ The line carries, besides the contract's keys:
   * ``roofline``: the method's flops (sum over rows of k_j (p+1) 2 m_j^3, executed iteration
     counts, true orders) per launch of the dominant kernel over its CUDA-event time, against
     the measured dense BF16 (= FP16) rate; the tensor-core work the engine executes for them
-    (15 FP16 slice products per product, 10 in GEMMs without level 4) is reported beside it as
+    (10 FP16 slice products per product) is reported beside it as
     ``executed_tensor_tflops``;
   * ``fp64_path``: the all-FP64 GPU path on the same input (median of --fp64-steps steps)
     and its error against the oracle on every row;
@@ -54,7 +54,7 @@ METRIC = "submatrices/s & TFLOP/s for sparse A^(-1/p) at rel.err<=1e-6 vs FP64 p
 UNIT = "submatrices/s"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (CUDA cores), nominal
-DTYPE_MIXED = "f16x5-slices/f32acc-per-level+f64"
+DTYPE_MIXED = "f16x4-slices/f32acc-per-level+f64"
 
 # The extra workloads of the default run: (name, workload, p, precision, root sign, rows
 # checked against the oracle (0 = every row), warm-up steps, timed steps).
@@ -344,8 +344,7 @@ def roofline_mixed(reps, pk, pk_kind):
             "work": "sum over rows of k_j (p+1) 2 m_j^3 (executed iterations, true orders)",
             "executed_tensor_tflops": executed / (kern_ms / 1e3) / 1e12,
             "executed_tensor_frac": executed / (kern_ms / 1e3) / 1e12 / peak,
-            "executed_work": "FP16 slice products (15, or 10 without level 4) x 2 m_j^3 per "
-                             "executed GEMM"}
+            "executed_work": "10 FP16 slice products x 2 m_j^3 per executed GEMM"}
 
 
 def roofline_fp64(reps):

@@ -58,16 +58,16 @@ typedef enum {
  * coupled iteration stay in its limit (X_inf = X_k M_k^(-1/p) from any iterate on), so a
  * low-precision phase followed by FP64 refinement leaves ~1e-3 (TF32) or ~1e-2 (BF16) for
  * p >= 2, and the tensor cores' FP32 accumulation truncates.  Each matrix is therefore split
- * into five FP16 planes of small integers whose level sums the FP32 accumulators hold
- * exactly (an error-free splitting in the manner of Ozaki et al.), ~39 significant bits;
+ * into four FP16 planes of 10-bit integers whose low level sums the FP32 accumulators hold
+ * exactly (an error-free splitting in the manner of Ozaki et al.), 40 bits below its scale;
  * FP64 stays for the gather, the scaling, the column output and its residual, the p = 1
  * refinement and the eigendecomposition fallback.
  */
 enum {
   SUBMAT_PREC_FP64 = 0,       /* coupled Newton iteration entirely in FP64 (CUDA cores)     */
   SUBMAT_PREC_MIXED_F16 = 1,  /* coupled Newton iteration on the tensor cores (tcgen05) with
-                                 every matrix split into five FP16 planes of small integers,
-                                 accumulated exactly per level (15 FP16 MMAs per product),
+                                 every matrix split into four FP16 planes of 10-bit integers,
+                                 accumulated per level (10 FP16 products per product),
                                  then the FP64 column residual check                       */
   SUBMAT_PREC_MIXED_F16_SYNC = 2  /* the same arithmetic on the legacy mma.sync tensor path
                                  (kept as the baseline of the tcgen05 engine)               */
@@ -136,19 +136,10 @@ typedef struct {
                               the tuned default.  The rows are ordered by decreasing m, so
                               each engine gets one contiguous run of the work queue and one
                               persistent launch                                           */
-  double level4_lo;        /* SUBMAT_PREC_MIXED_F16, tcgen05 engine: an iteration whose
-                              spectral interval [lo_k, 1] has lo_k >= level4_lo takes its
-                              GEMMs without the five level-4 slice products (s + t = 4, the
-                              terms of relative size ~2^-32; ten FP16 products per GEMM
-                              instead of fifteen, and plane 4 is not loaded); 0 drops them in
-                              every iteration, values above 1 in none; < 0 selects the
-                              default (SUBMAT_LEVEL4_LO)                                   */
 } submat_opts;
 
 /* Largest order the small-submatrix engine takes. */
 #define SUBMAT_SMALL_MAX_M 32
-/* Default of submat_opts.level4_lo. */
-#define SUBMAT_LEVEL4_LO 2.0
 
 typedef struct {
   int64_t n_rows;          /* submatrices processed by the last forward                  */
@@ -160,9 +151,9 @@ typedef struct {
   double max_resid;        /* largest FP64 column residual seen before the fallback      */
   double sum_m3;           /* sum over rows of m^3 (true sizes)                           */
   double flops_tensor;     /* tensor-core flops executed by the last forward: sum over
-                              GEMMs executed of (FP16 slice products: 15, or 10 without
-                              level 4) * 2 m_j^3 (true m_j; p GEMMs per iteration for
-                              p >= 2; two for p = 1, plus its final X product)           */
+                              rows of (GEMMs executed) * 10 FP16 slice products *
+                              2 m_j^3 (true m_j; p GEMMs per iteration for p >= 2;
+                              two for p = 1, plus its final X product)                   */
   double flops_fp64;       /* FP64 flops of the last forward (FP64 path: iterations;
                               mixed path: column refinement; both: fallback)             */
   float ms_kernel;         /* device time of the last forward's main (Newton) kernel,

@@ -22,7 +22,6 @@ LIB_PATH = os.path.join(_PKG, "libsubmat.so")
 
 SUBMAT_MAX_M = 1536
 SUBMAT_SMALL_MAX_M = 32
-SUBMAT_LEVEL4_LO = 2.0
 PREC_FP64 = 0
 PREC_MIXED_F16 = 1
 PREC_MIXED_F16_SYNC = 2
@@ -55,8 +54,7 @@ class Opts(ctypes.Structure):
                 ("kappa_max", ctypes.c_double), ("root_sign", ctypes.c_int32),
                 ("grad_deterministic", ctypes.c_int32), ("grad_wave_mib", ctypes.c_int32),
                 ("shard_count", ctypes.c_int32), ("shard_rank", ctypes.c_int32),
-                ("small_max_m", ctypes.c_int32), ("sync_max_m", ctypes.c_int32),
-                ("level4_lo", ctypes.c_double)]
+                ("small_max_m", ctypes.c_int32), ("sync_max_m", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -151,7 +149,7 @@ class Plan:
                  tol: float = 0.0, resid_tol: float = 0.0, refine_steps: int = -1,
                  use_graph: bool = True, kappa_max: float = 0.0, root_sign: int = -1,
                  grad_deterministic: bool = False, grad_wave_mib: int = 0, shard=(0, 1),
-                 small_max_m: int = -1, sync_max_m: int = -1, level4_lo: float = -1.0):
+                 small_max_m: int = -1, sync_max_m: int = -1):
         lib = load_library()
         self._lib = lib
         torch = _torch()
@@ -189,8 +187,6 @@ class Plan:
             o.small_max_m = int(small_max_m)
         if sync_max_m >= 0:
             o.sync_max_m = int(sync_max_m)
-        if level4_lo >= 0:
-            o.level4_lo = float(level4_lo)
         h = ctypes.c_void_p()
         _check(lib, lib.submat_plan(ctypes.byref(csr), int(p), ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -201,7 +197,6 @@ class Plan:
         self.root_sign = int(root_sign)
         self.small_max_m = int(o.small_max_m)
         self.sync_max_m = int(o.sync_max_m)
-        self.level4_lo = float(o.level4_lo)
         self.shard = (int(shard[0]), int(shard[1]))
         self.device = torch.device("cuda", torch.cuda.current_device())
         self._fwd_gen = 0              # forwards run on this plan (the backward's input)

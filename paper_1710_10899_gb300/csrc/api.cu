@@ -207,7 +207,6 @@ submat_status enqueue_forward(submat_plan_t P, const double* in, double* out, cu
   a.tm_a = P->tm_a;
   a.tm_b = P->tm_b;
   a.stall = P->d_stall;
-  a.level4_lo = (float)P->opts.level4_lo;
   CUDA_TRY(cudaMemcpyAsync(P->d_saved, in, (size_t)P->nnz * sizeof(double),
                            cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemsetAsync(P->d_ctr, 0, sizeof(DevCounters), s));
@@ -281,7 +280,6 @@ void submat_default_opts(submat_opts* o) {
   o->shard_rank = 0;
   o->small_max_m = kTunedSmallMaxM;
   o->sync_max_m = kTunedSyncMaxM;
-  o->level4_lo = SUBMAT_LEVEL4_LO;
 }
 
 const char* submat_status_string(submat_status s) {
@@ -339,7 +337,6 @@ static submat_status plan_impl(const submat_csr* csr, int32_t p, const submat_op
   }
   if (o.small_max_m < 0) o.small_max_m = kTunedSmallMaxM;
   if (o.sync_max_m < 0) o.sync_max_m = kTunedSyncMaxM;
-  if (!(o.level4_lo >= 0.0)) o.level4_lo = SUBMAT_LEVEL4_LO;
   if (o.small_max_m > small_engine_max_m())
     return fail(SUBMAT_EINVAL, "small_max_m exceeds SUBMAT_SMALL_MAX_M");
 

@@ -65,8 +65,6 @@ struct FwdArgs {
   const int32_t* stall;      // tcgen05 engine: nonzero makes every CTA first wait on a barrier
                              // that nothing signals (exercises the bounded wait; see
                              // submat_test_stall)
-  float level4_lo;           // tcgen05 engine: iterations with lo_k >= this skip the level-4
-                             // slice products
 };
 
 struct BwdArgs {

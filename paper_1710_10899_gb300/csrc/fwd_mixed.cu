@@ -15,32 +15,35 @@
 // Arithmetic.  Rounding errors made in any iteration persist in the coupled iteration's
 // limit, so every GEMM must be accurate to well below the 1e-6 target, and the tensor
 // cores' FP32 accumulation truncates (biased toward zero) when it rounds.  Each working
-// matrix is therefore held as five FP16 planes of small integers with one power-of-two
-// scale per matrix (an error-free splitting in the manner of Ozaki et al.; slices.cuh):
-//     A = 2^(E-7) sum_{s<5} q_s 2^(-8s),  |q0| <= 128, |q1..q4| <= 129,
-// about 39 significant bits relative to the largest entry (E is chosen tight: M's
-// eigenvalues lie in (0,1], those of T and of T^i M below bounds that follow from the step
-// constants; X's exponent is predicted from its last measured maximum).  A product is the sum over levels L = s + t <= 4 of
-// 2^(-8L) sum_{s+t=L} Q_s^A Q_t^B (15 FP16 MMAs per k-step, FP32 accumulation per level).
-// The products of these integers are exact, and every level-0 partial sum is an integer
-// below 2^14 K (plus 2^16 from the affine term below), so for K <= 1008 the tensor cores
-// accumulate level 0 exactly (level 1 multiplies q0 by a residual slice of either sign: its
-// sums stay far below 2^24 in practice, and its weight is 2^-8); levels 2..4 carry weights
-// 2^-16..2^-32.  Orders above 1008 raise every exponent by one (exp_bias), which keeps level 0
-// exact up to K = 4092.  The levels dropped (s + t >= 5) bound the normwise error of a
-// product near 2^-39 sqrt(K) of max|A| max|B|.  The epilogue combines the levels in
-// double-float (FP32 pairs) and re-splits the result.  (With four planes, the ~2^-31
-// per-product error, kept by every iteration, left ~6e-7 in the result; measured.)
+// matrix is therefore held as four FP16 planes of integers with one power-of-two scale per
+// matrix (an error-free splitting in the manner of Ozaki et al.; slices.cuh):
+//     A = 2^(E-9) sum_{s<4} q_s 2^(-10s),  |q0| <= 513, |q1..q3| <= 512,
+// 40 bits relative to the scale 2^E (E is chosen tight: M's eigenvalues lie in (0,1], those
+// of T and of T^i M below bounds that follow from the step constants, so 2^E bounds the
+// spectral norm; X's exponent bounds its largest entry, predicted from its last measured
+// maximum).  A product is the sum over levels L = s + t <= 3 of 2^(-10L) sum_{s+t=L} Q_s^A Q_t^B
+// (ten FP16 products per k-step, FP32 accumulation per level).  The products of these
+// integers are exact, and the level-0 and level-1 partial sums are integers bounded through
+// the operands' norms: with s0 = 2^(9-b) (b the exponent bias of slice_bias), every row of
+// A - alpha I (the affine term below, alpha <= p + 1) has 2-norm at most (p+1) s0 + sqrt(K)/2
+// in level-0 units and every column of a spectrally scaled B at most s0 + sqrt(K)/2, while a
+// residual slice is at most 512 in magnitude, so by Cauchy-Schwarz level 1 stays below
+// 513 sqrt(K) ((p+2) s0 + sqrt(K)) and level 0 far below that; slice_bias takes the smallest
+// b that keeps this under 2^24 (b = 0 up to K = 240 for p = 2, b = 1 up to about K = 950).
+// Levels 2 and 3 carry weights 2^-20 and 2^-30; the levels dropped (s + t >= 4) weigh 2^-40
+// and bound the normwise error of a product near 3 2^-40 K of the scales (2^-40 sqrt(K) for
+// slices of either sign).  The epilogue combines the levels in double-float (FP32 pairs)
+// and re-splits the result.
 //
 // GEMM engines (template parameter TC):
-//   TC = true  (default): tcgen05.mma kind::f16, M = 128, N = 96, the five level
-//              accumulators in one 480-column TMEM buffer, drained in phases (levels
+//   TC = true  (default): tcgen05.mma kind::f16, M = 128, N = 96, the four level
+//              accumulators in one 384-column TMEM buffer, drained in phases (levels
 //              combined into shared memory and TMEM released; scaling, slicing and the
 //              stores; the mirror images) so the next tile's MMAs overlap the later
 //              phases; operands moved by TMA (SWIZZLE_32B, 16-wide k-slices) through a
-//              3-stage mbarrier pipeline.  A full-width tile issues the fifteen plane
-//              products of a k-step as eight MMAs over B's concatenated planes (N up to
-//              240), and the affine term alpha Y (Y = B) enters the accumulators through
+//              3-stage mbarrier pipeline.  A full-width tile issues the ten plane
+//              products of a k-step as six MMAs over B's concatenated planes (N up to
+//              192), and the affine term alpha Y (Y = B) enters the accumulators through
 //              the level-0 A plane: on the k-steps of the tile's diagonal block the MMA
 //              warp subtracts the exact integer alpha' from its diagonal entries in the
 //              stage, so A_0 B_t adds -alpha' B_t to level t and the epilogue reads no Y.  Roles: warps 0-7 run the epilogue (two per TMEM
@@ -51,10 +54,10 @@
 //   TC = false: mma.sync m16n8k16 on 64 x 64 tiles with a cp.async pipeline (the legacy
 //              tensor path, kept as the baseline the tcgen05 engine is measured against).
 //
-// Working matrices live in a per-CTA global scratch: 35 planes of LD x LD halves per CTA
-// (LD = the plan's largest order padded to 64): two X buffers (p = 1) and three buffers for
-// M_k and the partial products, 5 planes each, the gathered S_j in FP64 in four planes'
-// space, and one plane for the carried vectors.  A submatrix of order m uses the
+// Working matrices live in a per-CTA global scratch: 29 planes of LD x LD halves per CTA
+// (LD = the plan's largest order padded to 16, at least 128): two X buffers (p = 1), three
+// buffers for M_k and the partial products and one spare, 4 planes each, the gathered S_j
+// in FP64 in four planes' space, and one plane for the carried vectors.  A submatrix of order m uses the
 // leading mp x mp block (mp = m padded to 16 for tcgen05, 64 for mma.sync); its padding
 // rows/columns stay exactly zero.  Rows of a tile beyond mp may hold older data: they only
 // reach output entries beyond mp, which are never stored.
@@ -71,8 +74,11 @@ namespace {
 using namespace slc;
 
 constexpr int E_M = 0;             // |M| <= 1 (eigenvalues of M_k lie in (0, 1])
-constexpr int kPlanesPerCta = 35;  // 6 matrices x 5 planes, 4 planes of room for S_j (FP64),
-                                   // 1 plane for the tracked vectors
+constexpr int kMatSlots = 6;       // X[2], three M / partial-product buffers, one spare
+constexpr int kSPlane = kMatSlots * NSL;          // S_j (FP64) in four planes' space
+constexpr int kVecPlane = kSPlane + 4;            // the tracked vectors
+constexpr int kPlanesPerCta = kVecPlane + 1;
+constexpr double kSliceProducts = NSL * (NSL + 1) / 2;   // FP16 products per GEMM (s + t < NSL)
 
 // Every product of the iteration has the form C = c (alpha Y - A Y), i.e. the step matrix
 // T = c (alpha I - A) applied to Y, with A = M_k and Y the B operand (all matrices are
@@ -94,17 +100,36 @@ struct GemmIO {     // what every GEMM call shares within one submatrix
   float* norm_part;  // ||.||_F^2 partial sums, one slot per writing warp (summed in order)
   unsigned* amax_s;
   float c, alpha;          // C = c (alpha Y - A B)
-  int lmax;                // tcgen05 engine: highest slice level L = s + t multiplied (3 or 4)
 };
 
 // Exponent for values bounded by b (with a relative margin for rounding).
 __device__ __forceinline__ int exp_of(float b) { return exp_bound(b * (1.f + 1e-6f)); }
 
-// Extra exponent for orders above 1008: with |q0| <= 64 every level-0 partial sum stays an
-// integer below 2^12 K + 2^14 < 2^24 up to K = 4092 (one of the ~39 bits is given up).  Level 0
-// matters most: for same-sign data (overlap matrices) its sums grow linearly with K, while
-// level 1 multiplies q0 by a rounding residual of either sign and grows like sqrt(K).
-__device__ __forceinline__ int exp_bias(int mp) { return mp > 1008 ? 1 : 0; }
+// Exponent bias b of the M / partial-product matrices of an order-mp row (entries then
+// scale to |q0| <= 2^(9-b)): the smallest b for which alpha' = alpha 2^(9-b) stays an FP16
+// integer next to q0 (alpha <= p + 1) and the level-0 / level-1 partial sums of every
+// product stay integers below 2^24 (the bounds of the file header).
+__device__ __forceinline__ int slice_bias(int mp, int p) {
+  const float rk = sqrtf((float)mp);
+  for (int b = 0; b < 3; ++b) {
+    const float s0 = ldexpf(1.f, Q0B - b);
+    if ((float)(p + 1) * s0 <= 2048.f &&
+        513.f * rk * ((float)(p + 2) * s0 + rk) < 16777216.f)
+      return b;
+  }
+  return 3;
+}
+// Exponent bias of the X matrices (p = 1; A = M_k with bias bm): X's exponent bounds its
+// entries, not its rows' 2-norms, so a column of X may reach s0 sqrt(K) in level-0 units.
+__device__ __forceinline__ int slice_bias_x(int mp, int bm) {
+  const float rk = sqrtf((float)mp), k = (float)mp;
+  const float sa = 2.f * ldexpf(1.f, Q0B - bm) + 0.5f * rk;   // rows of M - alpha I, alpha <= 2
+  for (int b = 0; b < 12; ++b) {
+    const float sx = ldexpf(1.f, Q0B - b) + 0.5f;
+    if (sa * sx * rk < 16777216.f && 513.f * rk * sa + 513.f * sx * k < 16777216.f) return b;
+  }
+  return 12;
+}
 
 // Slices of 8 consecutive values -> one 16-byte store per plane.
 __device__ __forceinline__ void store8_slices(__half* q, size_t plane, size_t idx0,
@@ -200,7 +225,7 @@ __device__ void matvec_slices_f32(const __half* q, size_t plane, int ld, float s
 #pragma unroll
           for (int k = 0; k < NP; ++k) {
             v = fmaf(__half2float(reinterpret_cast<const __half*>(&raw[r][k])[c]), w, v);
-            w *= (1.f / 256.f);
+            w *= kRadInv;
           }
           acc[r] = fmaf(v, xv[c], acc[r]);
         }
@@ -217,7 +242,7 @@ __device__ void matvec_slices_f32(const __half* q, size_t plane, int ld, float s
 // One pass over the sliced A (scale exponent e) for two products: out[i] = sum_k A(i,k) x[k]
 // in FP64 from x given as double-floats (xh, xl), and uo[i] = sum_k A(i,k) u[k] in FP32; all
 // vectors zero beyond m up to mp, i < m.  The planes' integers recombine exactly
-// (a = q0 2^8 + q1, b = q2 2^16 + q3 2^8 + q4, A = 2^(e-15) (a + 2^-24 b)) and the products
+// (a = q0 2^10 + q1, b = q2 2^10 + q3, A = 2^(e-19) (a + 2^-20 b)) and the products
 // a xh are accumulated error-free in double-float, so out keeps about 44 bits.  Each warp
 // takes RW rows at a time, eight consecutive columns per lane.
 template <int RW = 2, int BAR = 0, bool U = true>
@@ -225,7 +250,7 @@ __device__ void matvec2_slices(const __half* q, size_t plane, int ld, int e, con
                                const float* xl, double* out, const float* u, float* uo, int m,
                                int mp) {
   const int lane = threadIdx.x & 31, warp = grp_warp<BAR>();
-  const double sc = ldexp(1.0, e - 15);
+  const double sc = ldexp(1.0, e - Q0B - 10);
   for (int i0 = warp * RW; i0 < m; i0 += grp_warps<BAR>() * RW) {
     float sh[RW], sl[RW], su[RW];
 #pragma unroll
@@ -247,14 +272,14 @@ __device__ void matvec2_slices(const __half* q, size_t plane, int ld, int e, con
 #pragma unroll
           for (int k = 0; k < NSL; ++k)
             qq[k] = __half2float(reinterpret_cast<const __half*>(&raw[r][k])[c]);
-          const float a = __fmaf_rn(qq[0], 256.f, qq[1]);
-          const float b = __fmaf_rn(qq[2], 65536.f, __fmaf_rn(qq[3], 256.f, qq[4]));
+          const float a = __fmaf_rn(qq[0], kRad, qq[1]);
+          const float b = __fmaf_rn(qq[2], kRad, qq[3]);
           const float pr = __fmul_rn(a, x);
           const float pe = __fmaf_rn(a, x, -pr);          // a x - pr exactly
           float t;
           two_sum(sh[r], pr, sh[r], t);
-          sl[r] = __fadd_rn(sl[r], __fadd_rn(t, __fmaf_rn(a, xlo, __fmaf_rn(b * (1.f / 16777216.f), x, pe))));
-          if (U) su[r] = __fmaf_rn(__fmaf_rn(qq[2], 1.f / 256.f, a), uv, su[r]);   // FP32, 3 planes
+          sl[r] = __fadd_rn(sl[r], __fadd_rn(t, __fmaf_rn(a, xlo, __fmaf_rn(b * (kRadInv * kRadInv), x, pe))));
+          if (U) su[r] = __fmaf_rn(__fmaf_rn(qq[2], kRadInv, a), uv, su[r]);   // FP32, 3 planes
         }
       }
     }
@@ -322,7 +347,7 @@ __device__ void vec_task(const VecTask& v) {
         continue;
       }
     } else {
-      matvec_slices_f32<3, 8, BAR>(v.q, v.plane, v.ld, ldexpf(1.f, v.e - 7), v.u, v.t, v.m, v.mp);
+      matvec_slices_f32<3, 8, BAR>(v.q, v.plane, v.ld, ldexpf(1.f, v.e - Q0B), v.u, v.t, v.m, v.mp);
     }
     for (int i = gt; i < v.m; i += gn) v.u[i] = cf * (af * v.u[i] - v.t[i]);
     grp_sync<BAR>();
@@ -365,7 +390,7 @@ __device__ void taylor_final(const VecTask& v, int Jy, int Ju, double* ay, float
         matvec2_slices<RWY, 0, true>(v.q, v.plane, v.ld, v.e, v.yh, v.yl, v.my, au, v.t, v.m, v.mp);
         for (int i = gt; i < v.m; i += gn) ay[i] = cj[j] * v.y[i] + (ay[i] - v.my[i]);
       } else {
-        matvec_slices_f32<3, 8, 0>(v.q, v.plane, v.ld, ldexpf(1.f, v.e - 7), au, v.t, v.m, v.mp);
+        matvec_slices_f32<3, 8, 0>(v.q, v.plane, v.ld, ldexpf(1.f, v.e - Q0B), au, v.t, v.m, v.mp);
       }
       for (int i = gt; i < v.m; i += gn) au[i] = (float)cj[j] * v.u[i] + (au[i] - v.t[i]);
       __syncthreads();
@@ -420,7 +445,7 @@ __device__ float start_lo_slices(const __half* q, size_t plane, int ld, int e, i
   __syncthreads();
   float nb = 1.f;
   for (int t = 0; t < kStartLoSteps; ++t) {
-    matvec_slices_f32<2, 8>(q, plane, ld, ldexpf(1.f, e - 7), a_s, b_s, m, mp);   // b = M_0 a
+    matvec_slices_f32<2, 8>(q, plane, ld, ldexpf(1.f, e - Q0B), a_s, b_s, m, mp);   // b = M_0 a
     float part = 0.f;
     for (int i = tid; i < m; i += blockDim.x) {
       const float d = a_s[i] - b_s[i];
@@ -448,32 +473,33 @@ __device__ float start_lo_slices(const __half* q, size_t plane, int ld, int e, i
 // Output tiles of 128 rows x 96 columns (the last column tile of a row block is 16 to 96
 // wide: padded orders are multiples of 16).  A tcgen05.mma costs a fixed ~45 cycles below
 // N ~ 96 (measured), so 96-wide tiles keep the tensor pipe on the work instead of the
-// overhead.  The five 96-column level accumulators fill one 480-column TMEM buffer; the
+// overhead.  The four 96-column level accumulators fill one 384-column TMEM buffer; the
 // epilogue drains it in phases: phase 1 (a thread per TMEM lane, i.e. per tile row)
 // combines the levels into double-floats staged in shared memory and releases TMEM, so the
 // next tile's MMAs run during the rest; phase 2 (the affine step, slicing and stores) maps
 // consecutive threads to consecutive 8-column chunks of a row, so a warp's global loads and
 // stores cover whole row segments instead of 32 rows; phase 3 writes the mirror images of
 // the entries that fall in skipped tiles (see tc_skip) from the slices left in shared
-// memory (the last plane re-read from C), a thread per tile row, so that those stores are
+// memory, a thread per tile row, so that those stores are
 // contiguous too.  Operands move by TMA in 16-wide k-slices (32-byte rows, SWIZZLE_32B)
 // through a 3-stage mbarrier pipeline.
 constexpr int TC_M = 128, TC_N = 96, TC_K = 16;        // tile and k-slice
 constexpr int TC_STAGES = 3;
 constexpr int TC_A_PLANE = TC_M * TC_K * 2;            // 4096 B
 constexpr int TC_B_PLANE = TC_N * TC_K * 2;            // 3072 B
-constexpr int TC_STAGE_BYTES = NSL * (TC_A_PLANE + TC_B_PLANE);   // 35840 B
-constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 107520 B
+constexpr int TC_STAGE_BYTES = NSL * (TC_A_PLANE + TC_B_PLANE);   // 28672 B
+constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 86016 B
 // Staging area: per tile row, 4 x TC_CH 16-byte units (unit (k, ch) of row r holds the
-// double-floats of entries (r, 8 ch + 2k), (r, 8 ch + 2k + 1) after phase 1, and plane k < 4
+// double-floats of entries (r, 8 ch + 2k), (r, 8 ch + 2k + 1) after phase 1, and plane k
 // of entries (r, 8 ch .. 8 ch + 7) after phase 2), plus one unit of padding: the odd row
 // stride makes a thread-per-row access (phases 1 and 3) and a thread-per-chunk access
 // (phase 2) both free of bank conflicts.
 constexpr int TC_CH = TC_N / 8;                        // 8-column chunks per tile row (12)
 constexpr int TC_SROW = 4 * TC_CH + 1;                 // units per staged row (49)
 constexpr int TC_STAGING_BYTES = TC_M * TC_SROW * 16;  // 100352 B
-constexpr float kAlphaQuantum = 1.f / 64.f;            // alpha' = alpha 2^(7 - e) is an integer
-constexpr int TC_BUF_COLS = NSL * TC_N;                // 480 TMEM columns
+constexpr float kAlphaQuantum = 1.f / 64.f;            // alpha' = alpha 2^(9 - e) is an integer
+constexpr int TC_BUF_COLS = NSL * TC_N;                // 384 TMEM columns
+static_assert(TC_SROW >= NSL * TC_CH + 1, "staging units hold every plane of a chunk");
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;           // polls before a wait gives up
 constexpr uint32_t TC_TMEM_COLS = 512;
 static_assert(TC_BUF_COLS <= (int)TC_TMEM_COLS, "TMEM budget");
@@ -535,7 +561,7 @@ __device__ __forceinline__ bool mirror_needed(int i, int j, int tm) {
 }
 
 // Planes of the eight entries (row, j0..j0+7): one 16-byte store per plane to C, and the
-// planes 0..3 to the staging units su[0], su[TC_CH], ... when keep (for the mirror pass).
+// planes to the staging units su[0], su[TC_CH], ... when keep (for the mirror pass).
 __device__ __forceinline__ void store8_planes(__half* q, size_t plane, int ld, int row, int j0,
                                               const float* vh, const float* vl, int e,
                                               uint4* su, bool keep) {
@@ -552,7 +578,7 @@ __device__ __forceinline__ void store8_planes(__half* q, size_t plane, int ld, i
   for (int k = 0; k < NSL; ++k) {
     const uint4 v = *reinterpret_cast<const uint4*>(out[k]);
     *reinterpret_cast<uint4*>(q + k * plane + idx0) = v;
-    if (keep && k < 4) su[k * TC_CH] = v;
+    if (keep) su[k * TC_CH] = v;
   }
 }
 
@@ -563,38 +589,18 @@ __device__ __forceinline__ int sw32_index(int q, int k) {
   return q * TC_K + (((k >> 3) ^ ((q >> 2) & 1)) << 3) + (k & 7);
 }
 
-// The MMAs of one k-step.  A full-width tile (N = 96) concatenates B's planes: the five B
+// The MMAs of one k-step.  A full-width tile (N = 96) concatenates B's planes: the four B
 // planes of a stage lie back to back (96 rows each), and level L = s + t of A_s B_t sits at
 // TMEM columns 96 L, so A_s times B planes t0..t1 is one MMA with N = 96 (t1 - t0 + 1) whose
-// output columns start at 96 (s + t0).  The fifteen plane products become eight MMAs (N = 240,
-// 240, 192, 192, 144, 144, 192, 96), each reading its A plane once.  A last tile narrower
-// than 64 columns issues the fifteen products separately with N = nw.
+// output columns start at 96 (s + t0).  The ten plane products (s + t <= 3) become six MMAs
+// (N = 192, 192, 144, 144, 192, 96), each reading its A plane once.  A last tile narrower
+// than 64 columns issues the ten products separately with N = nw.
 __device__ __forceinline__ void mma_kstep_full(uint32_t d0, uint64_t da0, uint64_t db0,
                                                uint32_t acc0) {
-  constexpr uint32_t i240 = tc::idesc_f16(TC_M, 240), i192 = tc::idesc_f16(TC_M, 192),
-                     i144 = tc::idesc_f16(TC_M, 144), i96 = tc::idesc_f16(TC_M, 96);
-  constexpr uint64_t PA = TC_A_PLANE >> 4, RB = (TC_K * 2) >> 4;   // 16-byte units
-  // s = 0: B rows 0..479 -> columns 0..479 (overwrite at the first k-step)
-  tc::mma_f16(d0 + 0, da0, db0 + 0 * RB, i240, acc0);
-  tc::mma_f16(d0 + 240, da0, db0 + 240 * RB, i240, acc0);
-  // s = 1: B rows 0..383 -> columns 96..479
-  tc::mma_f16(d0 + 96, da0 + PA, db0 + 0 * RB, i192, 1u);
-  tc::mma_f16(d0 + 288, da0 + PA, db0 + 192 * RB, i192, 1u);
-  // s = 2: B rows 0..287 -> columns 192..479
-  tc::mma_f16(d0 + 192, da0 + 2 * PA, db0 + 0 * RB, i144, 1u);
-  tc::mma_f16(d0 + 336, da0 + 2 * PA, db0 + 144 * RB, i144, 1u);
-  // s = 3: B rows 0..191 -> columns 288..479; s = 4: B rows 0..95 -> columns 384..479
-  tc::mma_f16(d0 + 288, da0 + 3 * PA, db0, i192, 1u);
-  tc::mma_f16(d0 + 384, da0 + 4 * PA, db0, i96, 1u);
-}
-// Levels 0..3 only (A_s B_t with s + t <= 3, planes 0..3): ten products as six MMAs
-// (N = 192, 192, 144, 144, 192, 96) into TMEM columns 0..383; level 4's columns are not
-// written and not read.
-__device__ __forceinline__ void mma_kstep_full_l3(uint32_t d0, uint64_t da0, uint64_t db0,
-                                                  uint32_t acc0) {
   constexpr uint32_t i192 = tc::idesc_f16(TC_M, 192), i144 = tc::idesc_f16(TC_M, 144),
                      i96 = tc::idesc_f16(TC_M, 96);
   constexpr uint64_t PA = TC_A_PLANE >> 4, RB = (TC_K * 2) >> 4;   // 16-byte units
+  static_assert(NSL == 4, "the MMA list below is written for four planes");
   // s = 0: B rows 0..383 -> columns 0..383 (overwrite at the first k-step)
   tc::mma_f16(d0 + 0, da0, db0 + 0 * RB, i192, acc0);
   tc::mma_f16(d0 + 192, da0, db0 + 192 * RB, i192, acc0);
@@ -605,12 +611,10 @@ __device__ __forceinline__ void mma_kstep_full_l3(uint32_t d0, uint64_t da0, uin
   tc::mma_f16(d0 + 192, da0 + 2 * PA, db0, i192, 1u);
   tc::mma_f16(d0 + 288, da0 + 3 * PA, db0, i96, 1u);
 }
-// Levels 0..LMAX as separate products of width N = nw.
-template <int LMAX>
 __device__ __forceinline__ void mma_kstep_narrow(uint32_t d0, uint64_t da0, uint64_t db0,
                                                  uint32_t idesc, uint32_t acc0) {
 #pragma unroll
-  for (int L = 0; L <= LMAX; ++L) {
+  for (int L = 0; L < NSL; ++L) {
 #pragma unroll
     for (int sa_i = 0; sa_i <= L; ++sa_i) {
       const uint64_t da = da0 + (uint64_t)((sa_i * TC_A_PLANE) >> 4);
@@ -632,8 +636,6 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
   const int mp = io.mp;
   const int ntm = (mp + TC_M - 1) / TC_M, ntn = (mp + TC_N - 1) / TC_N, KT = mp / TC_K;
   const int ntiles = tc_ntiles(ntm, ntn);
-  const bool l4 = io.lmax >= 4;                      // level 4 multiplied (all five planes)
-  const int np = l4 ? NSL : NSL - 1;
   // generic-proxy writes (planes, shared vectors) before async-proxy reads/writes
   tc::fence_proxy_async_global();
   tc::fence_proxy_async_shared();
@@ -661,12 +663,13 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
           }
           unsigned char* sa = c.stages + s * TC_STAGE_BYTES;
           unsigned char* sb = sa + NSL * TC_A_PLANE;
-          // planes 0..lmax of both operands (levels up to lmax use no others)
-          tc::mbar_arrive_expect_tx(&c.full[s], np * (TC_A_PLANE + TC_B_PLANE));
-          for (int q = 0; q < np; ++q)
+          tc::mbar_arrive_expect_tx(&c.full[s], TC_STAGE_BYTES);
+#pragma unroll
+          for (int q = 0; q < NSL; ++q)
             tc::tma_load_3d(sa + q * TC_A_PLANE, c.tm_a, kt * TC_K, tm * TC_M, A.plane0 + q,
                             &c.full[s]);
-          for (int q = 0; q < np; ++q)
+#pragma unroll
+          for (int q = 0; q < NSL; ++q)
             tc::tma_load_3d(sb + q * TC_B_PLANE, c.tm_b, kt * TC_K, tn * TC_N, B.plane0 + q,
                             &c.full[s]);
           ++st.pit;
@@ -675,15 +678,16 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
     }
   } else if (warp == TC_MMA_WARP) {
     if (lane == 0) {                                   // ---- MMA issuer
-      // -alpha' = -alpha 2^(7 - e_A), an integer below 2^11 (alpha is a multiple of 1/64)
-      const __half nz = __float2half_rn(-ldexpf(io.alpha, 7 - A.e));
+      // -alpha' = -alpha 2^(9 - e_A), an integer of at most 2^11 (alpha is a multiple of
+      // 1/64, e_A <= 3; slice_bias keeps (p + 1) 2^(9 - e_A) <= 2^11), next to the diagonal's
+      // q0 in [0, 513] (M_k is positive definite)
+      const __half nz = __float2half_rn(-ldexpf(io.alpha, Q0B - A.e));
       for (int t = 0; t < ntiles && !*c.abort_s; ++t) {
         int tm, tn;
         tc_tile(t, ntn, tm, tn);
         const int nw = min(TC_N, mp - tn * TC_N);      // 96, or 16..80 for the last tile
         // tiles of 64 columns or more take the concatenated MMAs at the full width (their
-        // extra columns, beyond nw, are never read): per k-step ~730 tensor cycles against
-        // ~780 for fifteen separate N = 80 products and ~720 for N = 64
+        // extra columns, beyond nw, are never read)
         const bool full = nw >= 64;
         const uint32_t idesc = tc::idesc_f16(TC_M, nw);
         // k-steps inside the tile's diagonal block carry the affine term
@@ -724,14 +728,10 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
           const uint64_t da0 = tc::desc_sw32(sa);
           const uint64_t db0 = tc::desc_sw32(sa + NSL * TC_A_PLANE);
           const uint32_t acc0 = kt != 0;               // the first k-step overwrites
-          if (full && l4)
+          if (full)
             mma_kstep_full(d0, da0, db0, acc0);
-          else if (full)
-            mma_kstep_full_l3(d0, da0, db0, acc0);
-          else if (l4)
-            mma_kstep_narrow<NSL - 1>(d0, da0, db0, idesc, acc0);
           else
-            mma_kstep_narrow<NSL - 2>(d0, da0, db0, idesc, acc0);
+            mma_kstep_narrow(d0, da0, db0, idesc, acc0);
           tc::mma_commit(&c.empty[s]);                 // frees the stage when these MMAs finish
           ++st.cit;
         }
@@ -746,9 +746,9 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
   } else {                                             // ---- epilogue (TMEM lanes 0..127)
     const int q4 = warp & 3, half = warp >> 2;
     const int etid = tid;                              // 0 .. 255 (warps 0..7)
-    // the level sums count in units of cscale = 2^(A.e + B.e - 14) and already hold
+    // the level sums count in units of cscale = 2^(A.e + B.e - 18) and already hold
     // A B - alpha Y (alpha' sits on the level-0 A plane's diagonal), so C = -c cscale w
-    const float c_s = -ldexpf(io.c, A.e + B.e - 14);
+    const float c_s = -ldexpf(io.c, A.e + B.e - 2 * Q0B);
     float nrm = 0.f, amax = 0.f;
     const int rt = q4 * 32 + lane;                    // phase 1: this thread's tile row
     for (int t = 0; t < ntiles; ++t) {
@@ -778,13 +778,7 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
         for (int c0 = cb; c0 < ce; c0 += 8) {          // warp-uniform bounds
           float acc[NSL][8];
 #pragma unroll
-          for (int L = 0; L < NSL - 1; ++L) tc::tmem_ld8(tbase + L * TC_N + c0, acc[L]);
-          if (l4) {
-            tc::tmem_ld8(tbase + (NSL - 1) * TC_N + c0, acc[NSL - 1]);
-          } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) acc[NSL - 1][k] = 0.f;
-          }
+          for (int L = 0; L < NSL; ++L) tc::tmem_ld8(tbase + L * TC_N + c0, acc[L]);
           tc::tmem_ld_wait();
 #pragma unroll
           for (int k2 = 0; k2 < 4; ++k2) {
@@ -793,10 +787,9 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
             for (int h = 0; h < 2; ++h) {
               const int k = 2 * k2 + h;
               float s0, e0, t, u;
-              two_sum(acc[0][k], acc[1][k] * (1.f / 256.f), s0, e0);
-              two_sum(s0, acc[2][k] * (1.f / 65536.f), t, u);
-              e0 = __fadd_rn(__fadd_rn(e0, u), __fmaf_rn(acc[4][k], 1.f / 4294967296.f,
-                                                         acc[3][k] * (1.f / 16777216.f)));
+              two_sum(acc[0][k], acc[1][k] * kRadInv, s0, e0);
+              two_sum(s0, acc[2][k] * (kRadInv * kRadInv), t, u);
+              e0 = __fadd_rn(__fadd_rn(e0, u), acc[3][k] * (kRadInv * kRadInv * kRadInv));
               float wh, wl;
               two_sum(t, e0, wh, wl);
               w4[2 * h] = wh;
@@ -871,11 +864,7 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
           const uint4* su = c.staging + r * TC_SROW + ch;
 #pragma unroll
           for (int k = 0; k < NSL; ++k) {
-            // planes 0..3 from the staging area, plane 4 from C (written in phase 2, before
-            // the group barrier)
-            const uint4 v = k < 4 ? su[k * TC_CH]
-                                  : *reinterpret_cast<const uint4*>(C.q + 4 * io.plane +
-                                                                    (size_t)row * io.ld + j0);
+            const uint4 v = su[k * TC_CH];            // the planes left by phase 2
             const __half* hv = reinterpret_cast<const __half*>(&v);
             __half* dst = C.q + k * io.plane + (size_t)j0 * io.ld + row;
 #pragma unroll
@@ -910,7 +899,7 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
 // ======================================================================================
 constexpr int BM = 64;             // CTA output tile (64 x 64)
 constexpr int BK = 32;             // k-slice per pipeline stage
-constexpr int SY_STAGES = 3;
+constexpr int SY_STAGES = 4;
 constexpr int A_LD = BK + 8;       // padded smem row (halves) of an A tile plane
 constexpr int B_LD = BM + 8;       // padded smem row (halves) of a B tile plane
 constexpr int A_PLANE = BM * A_LD;
@@ -958,7 +947,7 @@ __device__ void gemm_sync(Mat A, Mat B, Mat C, Mat Y, int flags, const GemmIO& i
   const int nt = mp / BM;
   const int KT = mp / BK;
   const size_t plane = io.plane;
-  const float cscale = ldexpf(1.f, A.e + B.e - 14);
+  const float cscale = ldexpf(1.f, A.e + B.e - 2 * Q0B);
   float nrm = 0.f;
   float amax = 0.f;
 
@@ -1051,7 +1040,7 @@ __device__ void gemm_sync(Mat A, Mat B, Mat C, Mat Y, int flags, const GemmIO& i
             const int i = i0 + wm * 32 + mt * 16 + g + h * 8;
             const int jj = j0 + wn * 16 + n * 8 + 2 * q + c2;
             const float lv[NSL] = {acc[0][mt][n][ci], acc[1][mt][n][ci], acc[2][mt][n][ci],
-                                   acc[3][mt][n][ci], acc[4][mt][n][ci]};
+                                   acc[3][mt][n][ci]};
             float vh, vl, yh, yl, oh, ol;
             combine_levels(lv, cscale, vh, vl);
             const size_t idx = (size_t)i * ld + jj;
@@ -1086,14 +1075,14 @@ __device__ void gemm_sync(Mat A, Mat B, Mat C, Mat Y, int flags, const GemmIO& i
 // Orders up to kSmallMaxM: every sliced matrix lives in shared memory (leading dimension
 // kSmallLD; 80-byte rows make the eight row addresses of an ldmatrix fall in distinct banks),
 // the gathered S_j in the CTA's global scratch.  A product of padded order mp (16 or 32) is
-// (mp/16) x (mp/8) warp tiles of 16 x 8, one per warp, each running the fifteen plane products
-// of every 16-wide k-step with mma.sync m16n8k16 into five per-level FP32 accumulators (the
+// (mp/16) x (mp/8) warp tiles of 16 x 8, one per warp, each running the ten plane products
+// of every 16-wide k-step with mma.sync m16n8k16 into four per-level FP32 accumulators (the
 // same exact level arithmetic as the other engines), then C = c (alpha Y - A B) from Y's
 // shared-memory planes.  Two CTAs of 256 threads share an SM.
 constexpr int kSmallMaxM = 32;
 constexpr int kSmallLD = 40;
-constexpr int kSmallPlanes = 26;           // X[2], three M / partial-product buffers, vectors
-constexpr int kSmallVecPlane = 25;
+constexpr int kSmallPlanes = 5 * NSL + 1;  // X[2], three M / partial-product buffers, vectors
+constexpr int kSmallVecPlane = 5 * NSL;
 constexpr int kSmallVmax = 64;             // length of the shared vectors y_s, v_s, w_s, R_s
 constexpr int kSmallCtasPerSm = 2;
 static_assert(kSmallMaxM == SUBMAT_SMALL_MAX_M, "the header's limit of the small engine");
@@ -1111,7 +1100,7 @@ __device__ void gemm_small(Mat A, Mat B, Mat C, Mat Y, int flags, const GemmIO& 
   const int mp = io.mp;
   const int ntn = mp / 8, ntiles = (mp / 16) * ntn;
   const size_t plane = io.plane;
-  const float cscale = ldexpf(1.f, A.e + B.e - 14);
+  const float cscale = ldexpf(1.f, A.e + B.e - 2 * Q0B);
   float nrm = 0.f, amax = 0.f;
   for (int t = warp; t < ntiles; t += kWarps) {
     const int i0 = (t / ntn) * 16, j0 = (t % ntn) * 8;
@@ -1136,7 +1125,7 @@ __device__ void gemm_small(Mat A, Mat B, Mat C, Mat Y, int flags, const GemmIO& 
 #pragma unroll
     for (int ci = 0; ci < 4; ++ci) {
       const int i = i0 + g + (ci >> 1) * 8, jj = j0 + 2 * q + (ci & 1);
-      const float lv[NSL] = {acc[0][ci], acc[1][ci], acc[2][ci], acc[3][ci], acc[4][ci]};
+      const float lv[NSL] = {acc[0][ci], acc[1][ci], acc[2][ci], acc[3][ci]};
       float vh, vl, yh, yl, oh, ol;
       combine_levels(lv, cscale, vh, vl);
       const size_t idx = (size_t)i * kSmallLD + jj;
@@ -1220,9 +1209,9 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
   const size_t plane = (size_t)LD * LD;
   char* scr = a.scratch + (size_t)blockIdx.x * a.scratch_stride;
   __half* hb = SMALL ? reinterpret_cast<__half*>(sm + kSmallVecBytes) : reinterpret_cast<__half*>(scr);
-  double* S = SMALL ? reinterpret_cast<double*>(scr) : reinterpret_cast<double*>(hb + 30 * plane);
+  double* S = SMALL ? reinterpret_cast<double*>(scr) : reinterpret_cast<double*>(hb + kSPlane * plane);
   const int plane_base = blockIdx.x * kPlanesPerCta;
-  const int vec_plane = SMALL ? kSmallVecPlane : 34;
+  const int vec_plane = SMALL ? kSmallVecPlane : kVecPlane;
 
   TcCtx tcx{};
   TcState tst;
@@ -1284,12 +1273,14 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
 
     // Two X buffers (p = 1 only) and three buffers for M_k and the partial products T^s M_k
     // (M_k is the A operand of all p products of an iteration and stays in place).
-    Mat X[2] = {{hb + 0 * NSL * plane, 0, plane_base + 0}, {hb + 1 * NSL * plane, 0, plane_base + 5}};
-    const int eb = exp_bias(mp);
+    Mat X[2] = {{hb + 0 * NSL * plane, 0, plane_base + 0 * NSL},
+                {hb + 1 * NSL * plane, 0, plane_base + 1 * NSL}};
+    const int eb = slice_bias(mp, p);          // M_k and the partial products
+    const int ebx = slice_bias_x(mp, eb);      // X (p = 1)
     const int e_m = E_M + eb;
-    Mat B3[3] = {{hb + 2 * NSL * plane, e_m, plane_base + 10},
-                 {hb + 3 * NSL * plane, e_m, plane_base + 15},
-                 {hb + 4 * NSL * plane, e_m, plane_base + 20}};
+    Mat B3[3] = {{hb + 2 * NSL * plane, e_m, plane_base + 2 * NSL},
+                 {hb + 3 * NSL * plane, e_m, plane_base + 3 * NSL},
+                 {hb + 4 * NSL * plane, e_m, plane_base + 4 * NSL}};
     // vectors carried for p >= 2 and their scratch, in the last plane (32 LD bytes)
     double* yg = reinterpret_cast<double*>(hb + vec_plane * plane);   // column pos of X_k
     float* ug = reinterpret_cast<float*>(yg + LD);               // residual vector
@@ -1372,7 +1363,7 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
     __threadfence();             // planes are read next through L2 (cp.async.cg / TMA)
     __syncthreads();
 
-    GemmIO io{mp, m, p, LD, plane, norm_part, amax_s, 0.f, 0.f, 4};
+    GemmIO io{mp, m, p, LD, plane, norm_part, amax_s, 0.f, 0.f};
     // vt: vector work to run with this GEMM (tcgen05: on the vector warps during this and
     // the iteration's later GEMMs; mma.sync: before the GEMM on all warps).  first / last:
     // the GEMM starts / ends an iteration's sequence (see gemm_tc).
@@ -1392,7 +1383,7 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
     };
 
     int xc = 0, mi = 0;
-    int n_prod = 0;            // FP16 slice products executed (15 or 10 per GEMM)
+    int n_gemm = 0;
     const float tol2 = (float)(a.tol * a.tol * (double)m);
     const float stag2 = 1e-4f * (float)m;       // (1e-2)^2 m
     int iters = 0;
@@ -1406,20 +1397,16 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
     while (!bad) {
       // p >= 2: close enough to I for the final Taylor step (see below)
       if (track && nrm2 <= kTaylorStop * kTaylorStop) break;
-      const float lo_k = fmaxf(lo, 1.f - sqrtf(nrm2));
-      const ScaledStep st = scaled_step(lo_k, p, kAlphaQuantum);
+      const ScaledStep st = scaled_step(fmaxf(lo, 1.f - sqrtf(nrm2)), p, kAlphaQuantum);
       io.c = st.c;
       io.alpha = st.alpha;
-      // tcgen05 engine: without the level-4 products once lo_k is high enough (a product's
-      // error enters the limit X_K M_K^(-1/p) scaled by about 1 / (p lambda_min(M_{k+1})))
-      io.lmax = (TC && lo_k >= a.level4_lo) ? 3 : 4;
       const Mat Mk = B3[mi];
       const VecTask vt = vec_of(Mk, (double)st.c, (double)st.alpha, false);
       if (track) {
         // the vector step runs with the first product below
       } else if (iters == 0) {
         // X_1 = T_0 (elementwise from M_0)
-        X[0].e = exp_of(st.tmax) + eb;
+        X[0].e = exp_of(st.tmax) + ebx;
         xmax = st.tmax;
         for (int e = tid; e < mp * mp8; e += blockDim.x) {
           const int i = e / mp8, j0 = (e % mp8) * 8;
@@ -1440,11 +1427,11 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
       } else {
         // X_{k+1} = c (alpha X_k - X_k M_k); X_k, T_k SPD and commuting with T_k <= tmax I,
         // so the largest entry (a diagonal one) grows at most by tmax
-        X[xc ^ 1].e = exp_of(xmax * st.tmax) + eb;
+        X[xc ^ 1].e = exp_of(xmax * st.tmax) + ebx;
         if (tid == 0) *amax_s = 0u;
         __syncthreads();
         if (!gemm(Mk, X[xc], X[xc ^ 1], X[xc], EPI_AMAX, nullptr)) { stop = true; break; }
-        n_prod += io.lmax >= 4 ? 15 : 10;
+        ++n_gemm;
         xmax = __uint_as_float(*amax_s);
         xc ^= 1;
       }
@@ -1458,7 +1445,7 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
           stop = true;
           break;
         }
-        n_prod += io.lmax >= 4 ? 15 : 10;
+        ++n_gemm;
         src = dst;
         dst = 3 - mi - dst;                     // the buffer that is neither M_k nor P_s
       }
@@ -1544,17 +1531,17 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
     } else if (!bad) {
       io.c = 1.f;                                // p = 1: X (2 I - M)
       io.alpha = 2.f;
-      X[xc ^ 1].e = exp_of(xmax * 2.f) + eb;
+      X[xc ^ 1].e = exp_of(xmax * 2.f) + ebx;
       if (tid == 0) *amax_s = 0u;
       __syncthreads();
       if (!gemm(B3[mi], X[xc], X[xc ^ 1], X[xc], EPI_AMAX, nullptr)) {
         pending = j;
         break;
       }
-      n_prod += io.lmax >= 4 ? 15 : 10;
+      ++n_gemm;
       xc ^= 1;
-      SliceLoad xl{X[xc].q, plane, LD, ldexp(1.0, X[xc].e - 7)};
-      const float xs = ldexpf(1.f, X[xc].e - 7);
+      SliceLoad xl{X[xc].q, plane, LD, ldexp(1.0, X[xc].e - Q0B)};
+      const float xs = ldexpf(1.f, X[xc].e - Q0B);
       resid = refine_column(xl, c, S, m, pos, p, a.refine_steps, y_s, v_s, w_s, red_s);
       if (a.sign > 0) {          // A^(1/1): column pos of S itself (the iteration still checks S)
         for (int i = tid; i < m; i += blockDim.x) y_s[i] = S[pos * m + i];
@@ -1580,8 +1567,8 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
       atomicAdd(&a.ctr->iters_sum, (unsigned long long)iters);
       atomic_max_nonneg(&a.ctr->resid_max_bits, resid);
       atomicAdd(&a.ctr->flops_fp64, refine_flops(m, p, a.refine_steps));
-      // fifteen FP16 slice products per GEMM, counted with the true order m
-      atomicAdd(&a.ctr->flops_tensor, (double)n_prod * 2.0 * (double)m * m * m);
+      // ten FP16 slice products per GEMM, counted with the true order m
+      atomicAdd(&a.ctr->flops_tensor, (double)n_gemm * kSliceProducts * 2.0 * (double)m * m * m);
       // the method's own count: (p+1) dense products of order m per iteration (+ p = 1's
       // final X product), whatever this engine executes for them
       atomicAdd(&a.ctr->flops_alg,

@@ -1,10 +1,10 @@
 // Integer-slice representation of the mixed path's working matrices (internal header).
 //
-// A matrix is held as NSL FP16 planes of small integers with one power-of-two scale,
-//     A = 2^(E-7) sum_{s<NSL} q_s 2^(-8s),  |q_0| <= 128, |q_s| <= 129 (s >= 1),
-// so that the tensor cores multiply the planes exactly and accumulate each level
-// L = s + t of a product exactly (see fwd_mixed.cu).  Planes are row-major with leading
-// dimension ld; plane s starts at q + s * plane.
+// A matrix is held as NSL = 4 FP16 planes of integers with one power-of-two scale,
+//     A = 2^(E-9) sum_{s<4} q_s 2^(-10s),  |q_0| <= 513, |q_s| <= 512 (s >= 1),
+// 40 bits below the scale 2^E, so that the tensor cores multiply the planes exactly and
+// accumulate the low levels L = s + t of a product exactly (see fwd_mixed.cu).  Planes are
+// row-major with leading dimension ld; plane s starts at q + s * plane.
 #pragma once
 #include <cuda_fp16.h>
 #include "common.cuh"
@@ -12,7 +12,10 @@
 namespace submat {
 namespace slc {
 
-constexpr int NSL = 5;              // integer slices per matrix (levels 0..NSL-1 are kept)
+constexpr int NSL = 4;              // integer slices per matrix
+constexpr int Q0B = 9;              // an entry of magnitude 2^E has q_0 = 2^Q0B
+constexpr float kRad = 1024.f;      // 2^10: weight ratio of consecutive slices
+constexpr float kRadInv = 1.f / 1024.f;
 
 // Knuth's TwoSum (no products, so no contraction hazards).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -21,17 +24,24 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Slices of v = hi + lo (|v| <= 2^e) as floats q[0..NSL).
+// Slices of v = hi + lo (|v| <= 2^e) as floats q[0..NSL): q_0 = rint(v 2^(9-e)), then the
+// remainder times 2^30, rounded to an integer (an error of at most one unit of q_3), is cut
+// into balanced base-1024 digits with integer operations, so no bit of the double-float is
+// lost to an FP32 rounding of the remainder.
 __device__ __forceinline__ void make_slices(float hi, float lo, int e, float* q) {
-  const float sc = ldexpf(1.f, 7 - e);
+  const float sc = ldexpf(1.f, Q0B - e);
   const float yh = hi * sc, yl = lo * sc;           // exact (power-of-two scaling)
-  q[0] = rintf(yh);
-  float r = __fadd_rn(__fsub_rn(yh, q[0]), yl) * 256.f;
-#pragma unroll
-  for (int s = 1; s < NSL; ++s) {
-    q[s] = rintf(r);
-    r = __fsub_rn(r, q[s]) * 256.f;
-  }
+  const float q0 = rintf(yh);
+  const float rh = __fsub_rn(yh, q0);               // exact: |rh| <= 1/2
+  int r = __float2int_rn(rh * 1073741824.f) + __float2int_rn(yl * 1073741824.f);
+  const int d3 = ((r + 512) & 1023) - 512;          // in [-512, 511]
+  r = (r - d3) >> 10;                               // exact: r - d3 is a multiple of 1024
+  const int d2 = ((r + 512) & 1023) - 512;
+  r = (r - d2) >> 10;
+  q[0] = q0;
+  q[1] = (float)r;                                  // |r| <= 2^29 / 2^20 + 1
+  q[2] = (float)d2;
+  q[3] = (float)d3;
 }
 
 __device__ __forceinline__ void put_slices(__half* q, size_t plane, size_t idx, float hi,
@@ -42,21 +52,17 @@ __device__ __forceinline__ void put_slices(__half* q, size_t plane, size_t idx, 
   for (int s = 0; s < NSL; ++s) q[s * plane + idx] = __float2half_rn(v[s]);
 }
 
-// v = 2^(cexp) sum_L 2^(-8L) acc_L as a double-float (hi, lo).
+// v = cscale sum_L 2^(-10L) acc_L (levels 0..3) as a double-float (hi, lo); levels 0..2
+// join error-free.
 __device__ __forceinline__ void combine_levels(const float* acc, float cscale, float& vh,
                                                float& vl) {
-  float s0 = acc[0], e0, t, u;
-  two_sum(s0, acc[1] * (1.f / 256.f), t, u);
-  s0 = t;
-  e0 = u;
-  two_sum(s0, acc[2] * (1.f / 65536.f), t, u);
-  s0 = t;
-  e0 = __fadd_rn(e0, u);
-  e0 = __fadd_rn(e0, acc[3] * (1.f / 16777216.f));
-  e0 = __fadd_rn(e0, acc[4] * (1.f / 4294967296.f));
-  two_sum(s0, e0, t, u);
-  vh = t * cscale;
-  vl = u * cscale;
+  float s0, e0, t, u;
+  two_sum(acc[0], acc[1] * kRadInv, s0, e0);
+  two_sum(s0, acc[2] * (kRadInv * kRadInv), t, u);
+  e0 = __fadd_rn(__fadd_rn(e0, u), acc[3] * (kRadInv * kRadInv * kRadInv));
+  two_sum(t, e0, vh, vl);
+  vh *= cscale;
+  vl *= cscale;
 }
 
 // ((p+1) d - v) / p for v = vh + vl, in double-float.
@@ -114,22 +120,23 @@ __device__ __forceinline__ void mul_df(float ah, float al, float bh, float bl, f
 }
 
 // Eight consecutive values of a sliced matrix (scale exponent e) as double-floats.  The
-// planes' integers recombine exactly: q0 2^8 + q1 < 2^16 and q2 2^16 + q3 2^8 + q4 < 2^24.
+// planes' integers recombine exactly: a = q0 2^10 + q1 and b = q2 2^10 + q3 stay below 2^20,
+// and v 2^(9-e) = a 2^-10 + b 2^-30.
 __device__ __forceinline__ void load8_df(const __half* q, size_t plane, size_t idx0, int e,
                                          float* vh, float* vl) {
   uint4 raw[NSL];
 #pragma unroll
   for (int k = 0; k < NSL; ++k) raw[k] = *reinterpret_cast<const uint4*>(q + k * plane + idx0);
-  const float sc = ldexpf(1.f, e - 7);
+  const float sc = ldexpf(1.f, e - Q0B);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     float qq[NSL];
 #pragma unroll
     for (int k = 0; k < NSL; ++k) qq[k] = __half2float(reinterpret_cast<const __half*>(&raw[k])[c]);
-    const float a = __fmaf_rn(qq[0], 256.f, qq[1]);
-    const float b = __fmaf_rn(qq[2], 65536.f, __fmaf_rn(qq[3], 256.f, qq[4]));
+    const float a = __fmaf_rn(qq[0], kRad, qq[1]);
+    const float b = __fmaf_rn(qq[2], kRad, qq[3]);
     float h, l;
-    two_sum(a * (1.f / 256.f), b * (1.f / 4294967296.f), h, l);
+    two_sum(a * kRadInv, b * (kRadInv * kRadInv * kRadInv), h, l);
     vh[c] = h * sc;
     vl[c] = l * sc;
   }
@@ -152,11 +159,11 @@ __device__ __forceinline__ void load1_df(const __half* q, size_t plane, size_t i
   float qq[NSL];
 #pragma unroll
   for (int k = 0; k < NSL; ++k) qq[k] = __half2float(q[k * plane + idx]);
-  const float a = __fmaf_rn(qq[0], 256.f, qq[1]);
-  const float b = __fmaf_rn(qq[2], 65536.f, __fmaf_rn(qq[3], 256.f, qq[4]));
-  const float sc = ldexpf(1.f, e - 7);
+  const float a = __fmaf_rn(qq[0], kRad, qq[1]);
+  const float b = __fmaf_rn(qq[2], kRad, qq[3]);
+  const float sc = ldexpf(1.f, e - Q0B);
   float h, l;
-  two_sum(a * (1.f / 256.f), b * (1.f / 4294967296.f), h, l);
+  two_sum(a * kRadInv, b * (kRadInv * kRadInv * kRadInv), h, l);
   vh = h * sc;
   vl = l * sc;
 }
@@ -173,25 +180,24 @@ struct SliceLoad {     // X(i,k) as double from the slices
   const __half* q;
   size_t plane;
   int ld;
-  double scale;        // 2^(e-7)
+  double scale;        // 2^(e-9)
   __device__ __forceinline__ double operator()(int i, int k) const {
     const size_t e = (size_t)i * ld + k;
-    const float a = __half2float(q[e]) + __half2float(q[plane + e]) * (1.f / 256.f);
-    const float b = __half2float(q[2 * plane + e]) * (1.f / 65536.f) +
-                    __half2float(q[3 * plane + e]) * (1.f / 16777216.f);
-    const float c = __half2float(q[4 * plane + e]) * (1.f / 4294967296.f);
-    return ((double)a + (double)b + (double)c) * scale;
+    const float a = __half2float(q[e]) + __half2float(q[plane + e]) * kRadInv;   // exact
+    const float b = (__half2float(q[2 * plane + e]) +
+                     __half2float(q[3 * plane + e]) * kRadInv) * (kRadInv * kRadInv);
+    return ((double)a + (double)b) * scale;
   }
 };
 
-struct SliceLoadF {    // leading 15 bits, FP32 (condition estimate)
+struct SliceLoadF {    // leading 20 bits, FP32 (condition estimate)
   const __half* q;
   size_t plane;
   int ld;
-  float scale;
+  float scale;         // 2^(e-9)
   __device__ __forceinline__ float operator()(int i, int k) const {
     const size_t e = (size_t)i * ld + k;
-    return (__half2float(q[e]) + __half2float(q[plane + e]) * (1.f / 256.f)) * scale;
+    return (__half2float(q[e]) + __half2float(q[plane + e]) * kRadInv) * scale;
   }
 };
 

@@ -45,7 +45,6 @@ def test_status_strings_and_defaults(lib):
     assert o.precision == pkg.PREC_MIXED_F16 and o.k_max == 40 and o.use_graph == 1
     assert o.root_sign == -1 and o.kappa_max == 100.0
     assert o.grad_deterministic == 0 and o.grad_wave_mib == 0
-    assert o.level4_lo == pkg.SUBMAT_LEVEL4_LO
 
 
 def _plan_status(lib, rowptr, colind, p=2):
@@ -194,9 +193,6 @@ def test_binding_constants_match_the_header():
     assert macros["SUBMAT_MAX_M"] == pkg.SUBMAT_MAX_M
     assert macros["SUBMAT_NOALLOC_MAX_M"] == pkg.SUBMAT_NOALLOC_MAX_M
     assert macros["SUBMAT_SMALL_MAX_M"] == pkg.SUBMAT_SMALL_MAX_M
-    fmacros = {k: float(v) for k, v in
-               re.findall(r"#define\s+(SUBMAT_[A-Z0-9_]+)\s+([0-9.eE+-]+)\s*$", text, flags=re.M)}
-    assert fmacros["SUBMAT_LEVEL4_LO"] == pkg.SUBMAT_LEVEL4_LO
 
 
 def _prototypes():

@@ -173,29 +173,6 @@ def test_engine_buckets(sm, buckets):
     assert rep["n_fallback"] == 0 and rep["n_rows"] == a.n
 
 
-@pytest.mark.parametrize("p", [2, 3])
-def test_level4_products(sm, p):
-    """The tcgen05 engine's GEMMs without the level-4 slice products: in no iteration
-    (level4_lo > 1, the default), from lo_k >= 0.5 on, and in every iteration (level4_lo = 0).
-    The first two meet the bar on every row of this workload; the third is ~10x less accurate
-    (about 5e-7 here), so its bar is looser.  The same iterations run in all three, and the
-    executed slice products drop from 15 to 10 per GEMM where level 4 is left out."""
-    a = wl.overlap_uniform(n=4096)
-    ref = oracle.pool.invroot(a.rowptr, a.colind, a.vals, p)
-    reps, errs = {}, {}
-    for l4 in (2.0, 0.5, 0.0):
-        plan, y = run(sm, a, p, "mixed", level4_lo=l4, small_max_m=0)
-        errs[l4] = row_errors(a, y, ref, range(a.n)).max()
-        reps[l4] = plan.report()
-        assert reps[l4]["n_fallback"] == 0 and reps[l4]["n_notspd"] == 0
-    assert errs[2.0] <= TOL["mixed"] and errs[0.5] <= TOL["mixed"]
-    assert errs[0.0] <= 10 * TOL["mixed"]
-    assert reps[2.0]["iters_sum"] == reps[0.0]["iters_sum"]
-    # every row runs on the tcgen05 engine (small_max_m = 0, no mma.sync bucket by default)
-    assert abs(reps[0.0]["flops_tensor"] / reps[2.0]["flops_tensor"] - 10 / 15) < 1e-12
-    assert reps[0.0]["flops_tensor"] < reps[0.5]["flops_tensor"] < reps[2.0]["flops_tensor"]
-
-
 def test_dense_pattern_equals_full_root(sm):
     import scipy.linalg as sl
     rng = np.random.default_rng(9)
