@@ -224,12 +224,13 @@ __device__ __forceinline__ void find_sorted_u(const int32_t* a, int len, const i
 // covers the rounding; any bound above the largest eigenvalue serves).  The extents of all
 // m pattern rows are loaded first, in parallel; then each warp takes one row at a time, with
 // the first 32 U entries of its next row already requested, and locates a row's entries in
-// R by interleaved bisections.  red_s: kRedDoubles doubles of shared memory.
-static __device__ double gather_submatrix(const int32_t* __restrict__ rowptr,
-                                   const int32_t* __restrict__ colind,
-                                   const double* __restrict__ vals, int j, int m,
-                                   int32_t* R_s, double* __restrict__ S, double* red_s) {
-  __shared__ int2 ext_s[SUBMAT_MAX_M];               // [rowptr[R_k], rowptr[R_k + 1])
+// R by interleaved bisections.  red_s: kRedDoubles doubles of shared memory; ext_s: m int2
+// of shared memory for the rows' extents [rowptr[R_k], rowptr[R_k + 1]).
+static __device__ double gather_rows(const int32_t* __restrict__ rowptr,
+                                     const int32_t* __restrict__ colind,
+                                     const double* __restrict__ vals, int j, int m,
+                                     int32_t* R_s, double* __restrict__ S, double* red_s,
+                                     int2* ext_s) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int base = rowptr[j];
   for (int k = tid; k < m; k += blockDim.x) {
@@ -291,6 +292,15 @@ static __device__ double gather_submatrix(const int32_t* __restrict__ rowptr,
   }
   __syncthreads();
   return lam * (1.0 + 1e-4);
+}
+
+// gather_rows with the extents in a static shared array of SUBMAT_MAX_M entries.
+static __device__ double gather_submatrix(const int32_t* __restrict__ rowptr,
+                                          const int32_t* __restrict__ colind,
+                                          const double* __restrict__ vals, int j, int m,
+                                          int32_t* R_s, double* __restrict__ S, double* red_s) {
+  __shared__ int2 ext_s[SUBMAT_MAX_M];
+  return gather_rows(rowptr, colind, vals, j, m, R_s, S, red_s, ext_s);
 }
 
 // Atomic max of a non-negative double (NaN counts as +inf).

@@ -41,7 +41,7 @@
 //              combined into shared memory and TMEM released; scaling, slicing and the
 //              stores; the mirror images) so the next tile's MMAs overlap the later
 //              phases; operands moved by TMA (SWIZZLE_32B, 16-wide k-slices) through a
-//              3-stage mbarrier pipeline.  A full-width tile issues the ten plane
+//              4-stage mbarrier pipeline.  A full-width tile issues the ten plane
 //              products of a k-step as six MMAs over B's concatenated planes (N up to
 //              192), and the affine term alpha Y (Y = B) enters the accumulators through
 //              the level-0 A plane: on the k-steps of the tile's diagonal block the MMA
@@ -482,13 +482,13 @@ __device__ float start_lo_slices(const __half* q, size_t plane, int ld, int e, i
 // the entries that fall in skipped tiles (see tc_skip) from the slices left in shared
 // memory, a thread per tile row, so that those stores are
 // contiguous too.  Operands move by TMA in 16-wide k-slices (32-byte rows, SWIZZLE_32B)
-// through a 3-stage mbarrier pipeline.
+// through a 4-stage mbarrier pipeline.
 constexpr int TC_M = 128, TC_N = 96, TC_K = 16;        // tile and k-slice
-constexpr int TC_STAGES = 3;
+constexpr int TC_STAGES = 4;
 constexpr int TC_A_PLANE = TC_M * TC_K * 2;            // 4096 B
 constexpr int TC_B_PLANE = TC_N * TC_K * 2;            // 3072 B
 constexpr int TC_STAGE_BYTES = NSL * (TC_A_PLANE + TC_B_PLANE);   // 28672 B
-constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 86016 B
+constexpr int TC_STAGE_AREA = TC_STAGES * TC_STAGE_BYTES;         // 114688 B
 // Staging area: per tile row, 4 x TC_CH 16-byte units (unit (k, ch) of row r holds the
 // double-floats of entries (r, 8 ch + 2k), (r, 8 ch + 2k + 1) after phase 1, and plane k
 // of entries (r, 8 ch .. 8 ch + 7) after phase 2), plus one unit of padding: the odd row
@@ -937,7 +937,7 @@ __device__ __forceinline__ void mma16816(float* c, const uint32_t* a, const uint
 }
 
 // C = A B (mp x mp, sliced, row-major ld).  All eight warps work on one 64 x 64 output tile
-// at a time (warps 2 x 4, 32 x 16 each), 3-stage cp.async pipeline over k.
+// at a time (warps 2 x 4, 32 x 16 each), 4-stage cp.async pipeline over k.
 __device__ void gemm_sync(Mat A, Mat B, Mat C, Mat Y, int flags, const GemmIO& io,
                           __half* smem) {
   const int tid = threadIdx.x;
@@ -1176,6 +1176,8 @@ constexpr size_t kVecBytes = 4 * SUBMAT_MAX_M * sizeof(double) + kRedDoubles * s
                              SUBMAT_MAX_M * sizeof(int32_t);
 static_assert(kVecBytes <= (size_t)SY_STAGE_AREA, "vector area must fit in the stage area");
 // the Taylor finish's vectors follow it (3 doubles and 5 floats per entry)
+static_assert(kVecBytes + SUBMAT_MAX_M * sizeof(int2) <= (size_t)TC_STAGE_AREA,
+              "the gather's row extents must fit in the idle stage area");
 static_assert(kVecBytes + 44 * (size_t)SUBMAT_MAX_M <= (size_t)SY_STAGE_AREA &&
                   kVecBytes + 44 * (size_t)SUBMAT_MAX_M <= (size_t)TC_STAGE_AREA + TC_STAGING_BYTES,
               "finish vectors must fit in the idle stage area");
@@ -1291,7 +1293,14 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
     double* ayg = reinterpret_cast<double*>(tg + LD);            // Horner accumulators of
     float* aug = reinterpret_cast<float*>(ayg + LD);             // the final step
 
-    const double lam = gather_submatrix(a.rowptr, a.colind, a.vals_in, j, m, R_s, S, red_s);
+    // the tcgen05 engine keeps the rows' extents in its idle stage area (no static shared
+    // array, which would leave no room for the fourth TMA stage)
+    double lam;
+    if constexpr (TC)
+      lam = gather_rows(a.rowptr, a.colind, a.vals_in, j, m, R_s, S, red_s,
+                        reinterpret_cast<int2*>(sm + kVecBytes));
+    else
+      lam = gather_submatrix(a.rowptr, a.colind, a.vals_in, j, m, R_s, S, red_s);
     const double inv_lam = 1.0 / lam;
 
     // M_0 = S / lambda_bar (leading mp x mp, eight consecutive columns per thread), in
