@@ -7,14 +7,14 @@
 // Device: NVIDIA GB300; p = 2; 7296 rows of one order per case; ms per forward
 // (median):
 //     m        small      sync   tcgen05
-//     8        1.897     6.596     4.485
-//    16        2.073     7.461     4.742
-//    24        2.391     8.194     5.705
-//    32        2.509     8.407     5.951
-//    48            -     9.307     7.140
-//    64            -     9.939     8.151
-//    96            -    31.192    11.897
-//   128            -    33.562    16.978
+//     8        1.904     6.145     4.508
+//    16        2.047     6.788     4.716
+//    24        2.291     7.345     5.517
+//    32        2.380     7.573     5.630
+//    48            -     8.371     6.596
+//    64            -     8.975     7.806
+//    96            -    25.950    11.104
+//   128            -    27.932    15.184
 #pragma once
 namespace submat {
 constexpr int kTunedSmallMaxM = 32;
