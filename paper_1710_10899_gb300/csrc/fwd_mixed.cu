@@ -676,72 +676,79 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
         }
       }
     }
-  } else if (warp == TC_MMA_WARP) {
-    if (lane == 0) {                                   // ---- MMA issuer
-      // -alpha' = -alpha 2^(9 - e_A), an integer of at most 2^11 (alpha is a multiple of
-      // 1/64, e_A <= 3; slice_bias keeps (p + 1) 2^(9 - e_A) <= 2^11), next to the diagonal's
-      // q0 in [0, 513] (M_k is positive definite)
-      const __half nz = __float2half_rn(-ldexpf(io.alpha, Q0B - A.e));
-      for (int t = 0; t < ntiles && !*c.abort_s; ++t) {
-        int tm, tn;
-        tc_tile(t, ntn, tm, tn);
-        const int nw = min(TC_N, mp - tn * TC_N);      // 96, or 16..80 for the last tile
-        // tiles of 64 columns or more take the concatenated MMAs at the full width (their
-        // extra columns, beyond nw, are never read)
-        const bool full = nw >= 64;
-        const uint32_t idesc = tc::idesc_f16(TC_M, nw);
-        // k-steps inside the tile's diagonal block carry the affine term
-        const int kd0 = tm * (TC_M / TC_K), kd1 = min(KT, kd0 + TC_M / TC_K);
-        // the single accumulator buffer is free once the epilogue has read the previous tile
-        if (st.tmt >= 1 && !tc::mbar_wait(c.tmem_empty, (st.tmt - 1) & 1, TC_WAIT_LIMIT)) {
-          *c.abort_s = 1;
+  } else if (warp == TC_MMA_WARP) {                    // ---- MMA issuer
+    // The whole warp runs the loops (waits, votes and the diagonal patch); lane 0 issues the
+    // MMAs and commits.  Every wait is taken by all lanes and combined by a vote, so the
+    // warp's control flow stays uniform even if a wait gives up.
+    // -alpha' = -alpha 2^(9 - e_A), an integer of at most 2^11 (alpha is a multiple of
+    // 1/64, e_A <= 3; slice_bias keeps (p + 1) 2^(9 - e_A) <= 2^11), next to the diagonal's
+    // q0 in [0, 513] (M_k is positive definite)
+    const __half nz = __float2half_rn(-ldexpf(io.alpha, Q0B - A.e));
+    for (int t = 0; t < ntiles; ++t) {
+      if (__any_sync(0xffffffffu, *c.abort_s != 0)) break;
+      int tm, tn;
+      tc_tile(t, ntn, tm, tn);
+      const int nw = min(TC_N, mp - tn * TC_N);        // 96, or 16..80 for the last tile
+      // tiles of 64 columns or more take the concatenated MMAs at the full width (their
+      // extra columns, beyond nw, are never read)
+      const bool full = nw >= 64;
+      const uint32_t idesc = tc::idesc_f16(TC_M, nw);
+      // k-steps inside the tile's diagonal block carry the affine term
+      const int kd0 = tm * (TC_M / TC_K), kd1 = min(KT, kd0 + TC_M / TC_K);
+      // the single accumulator buffer is free once the epilogue has read the previous tile
+      const bool freed = st.tmt < 1 || tc::mbar_wait(c.tmem_empty, (st.tmt - 1) & 1, TC_WAIT_LIMIT);
+      if (!__all_sync(0xffffffffu, freed)) {
+        *c.abort_s = 1;
+        break;
+      }
+      tc::tc_fence_after();
+      const uint32_t d0 = c.tmem;
+      bool ok = true;
+      for (int kt = 0; kt < KT; ++kt) {
+        const uint32_t s = st.cit % TC_STAGES;
+        const bool got = tc::mbar_wait(&c.full[s], (st.cit / TC_STAGES) & 1, TC_WAIT_LIMIT);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
           break;
         }
         tc::tc_fence_after();
-        const uint32_t d0 = c.tmem;
-        bool ok = true;
-        for (int kt = 0; kt < KT; ++kt) {
-          const uint32_t s = st.cit % TC_STAGES;
-          if (!tc::mbar_wait(&c.full[s], (st.cit / TC_STAGES) & 1, TC_WAIT_LIMIT)) {
-            ok = false;
-            break;
+        if (kt >= kd0 && kt < kd1) {
+          // the affine term: A_0 - alpha' I on this k-step's 16 diagonal entries of the
+          // stage's level-0 A plane (integers of at most 2^11 stay exact in FP16), so the
+          // products A_0 B_t add -alpha' B_t to level t; lane k patches entry k and hands
+          // its write to the tensor core's proxy before lane 0 issues
+          if (lane < TC_K) {
+            __half* a0 = reinterpret_cast<__half*>(c.stages + s * TC_STAGE_BYTES);
+            const int idx = sw32_index((kt - kd0) * TC_K + lane, lane);
+            a0[idx] = __hadd(a0[idx], nz);
+            tc::fence_proxy_async_shared();
           }
-          tc::tc_fence_after();
+          __syncwarp();
+        }
+        if (lane == 0) {
           // operand descriptors of the stage; every offset added below is a compile-time
           // constant added to the 14-bit start-address field (no carry: shared addresses
           // stay below 2^18 bytes)
-          if (kt >= kd0 && kt < kd1) {
-            // the affine term: A_0 - alpha' I on this k-step's 16 diagonal entries of the
-            // stage's level-0 A plane (integers below 2^11 stay exact in FP16), so the
-            // products A_0 B_t add -alpha' B_t to level t; then hand the plane back to the
-            // tensor core's proxy
-            __half* a0 = reinterpret_cast<__half*>(c.stages + s * TC_STAGE_BYTES);
-            const int o = (kt - kd0) * TC_K;
-#pragma unroll
-            for (int k = 0; k < TC_K; ++k) {
-              const int idx = sw32_index(o + k, k);
-              a0[idx] = __hadd(a0[idx], nz);
-            }
-            tc::fence_proxy_async_shared();
-          }
           const uint32_t sa = tc::saddr(c.stages + s * TC_STAGE_BYTES);
           const uint64_t da0 = tc::desc_sw32(sa);
           const uint64_t db0 = tc::desc_sw32(sa + NSL * TC_A_PLANE);
-          const uint32_t acc0 = kt != 0;               // the first k-step overwrites
+          const uint32_t acc0 = kt != 0;             // the first k-step overwrites
           if (full)
             mma_kstep_full(d0, da0, db0, acc0);
           else
             mma_kstep_narrow(d0, da0, db0, idesc, acc0);
-          tc::mma_commit(&c.empty[s]);                 // frees the stage when these MMAs finish
-          ++st.cit;
+          tc::mma_commit(&c.empty[s]);               // frees the stage when these MMAs finish
         }
-        if (!ok) {
-          *c.abort_s = 1;
-          break;
-        }
-        tc::mma_commit(c.tmem_full);                   // accumulators of tile t ready
-        ++st.tmt;
+        __syncwarp();
+        ++st.cit;
       }
+      if (!ok) {
+        *c.abort_s = 1;
+        break;
+      }
+      if (lane == 0) tc::mma_commit(c.tmem_full);     // accumulators of tile t ready
+      __syncwarp();
+      ++st.tmt;
     }
   } else {                                             // ---- epilogue (TMEM lanes 0..127)
     const int q4 = warp & 3, half = warp >> 2;
