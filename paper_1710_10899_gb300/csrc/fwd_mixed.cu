@@ -467,6 +467,54 @@ __device__ float start_lo_slices(const __half* q, size_t plane, int ld, int e, i
   return 1.f - nb;
 }
 
+// start_lo_slices with M_0 held in shared memory as FP32 (row stride mp; rows and columns
+// beyond m zero): the same power steps, each warp taking four rows at a time.
+__device__ float start_lo_smem(const float* __restrict__ Mf, int m, int mp, float* a_s,
+                               float* b_s, float* red_s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nwarps();
+  const float inv_n = rsqrtf((float)m);
+  for (int i = tid; i < mp; i += blockDim.x) {
+    a_s[i] = i < m ? ((i % 3 == 0) ? inv_n : -inv_n) : 0.f;
+    b_s[i] = 0.f;
+  }
+  __syncthreads();
+  float nb = 1.f;
+  for (int t = 0; t < kStartLoSteps; ++t) {
+    for (int i0 = warp * 4; i0 < m; i0 += nw * 4) {          // b = M_0 a
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int jj = lane; jj < mp; jj += 32) {
+        const float av = a_s[jj];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r] = fmaf(Mf[min(i0 + r, m - 1) * mp + jj], av, acc[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float v = warp_sum_f(acc[r]);
+        if (lane == 0 && i0 + r < m) b_s[i0 + r] = v;
+      }
+    }
+    __syncthreads();
+    float part = 0.f;
+    for (int i = tid; i < m; i += blockDim.x) {
+      const float d = a_s[i] - b_s[i];
+      b_s[i] = d;
+      part += d * d;
+    }
+    part = warp_sum_f(part);
+    if (lane == 0) red_s[warp] = part;
+    __syncthreads();
+    float tot = 0.f;
+    for (int w = 0; w < nw; ++w) tot += red_s[w];
+    nb = sqrtf(tot);
+    if (nb == 0.f) return 1.f;      // a lies in M_0's eigenvalue 1 (m = 1): Newton steps
+    if (!(nb > 0.f)) return kLoMin;
+    const float inv = 1.f / nb;
+    for (int i = tid; i < m; i += blockDim.x) a_s[i] = b_s[i] * inv;
+    __syncthreads();
+  }
+  return 1.f - nb;
+}
+
 // ======================================================================================
 // tcgen05 engine
 // ======================================================================================
@@ -1185,6 +1233,9 @@ static_assert(kVecBytes <= (size_t)SY_STAGE_AREA, "vector area must fit in the s
 // the Taylor finish's vectors follow it (3 doubles and 5 floats per entry)
 static_assert(kVecBytes + SUBMAT_MAX_M * sizeof(int2) <= (size_t)TC_STAGE_AREA,
               "the gather's row extents must fit in the idle stage area");
+static_assert(kVecBytes % 16 == 0, "16-byte aligned areas after the vectors");
+// tcgen05 engine: room for M_0 in FP32 after the vectors, in the idle stage and staging areas
+constexpr size_t kMfBytes = (size_t)TC_STAGE_AREA + TC_STAGING_BYTES - kVecBytes;
 static_assert(kVecBytes + 44 * (size_t)SUBMAT_MAX_M <= (size_t)SY_STAGE_AREA &&
                   kVecBytes + 44 * (size_t)SUBMAT_MAX_M <= (size_t)TC_STAGE_AREA + TC_STAGING_BYTES,
               "finish vectors must fit in the idle stage area");
@@ -1312,6 +1363,12 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
 
     // M_0 = S / lambda_bar (leading mp x mp, eight consecutive columns per thread), in
     // double-float FP32 from the integer split of the FP64 values; also ||M_0 - I||_F^2.
+    // The tcgen05 engine also keeps M_0's leading FP32 words in its idle stage area, when
+    // they fit, for the power steps below.
+    float* Mf = nullptr;
+    if constexpr (TC) {
+      if ((size_t)mp * mp * sizeof(float) <= kMfBytes) Mf = reinterpret_cast<float*>(sm + kVecBytes);
+    }
     const int mp8 = mp / 8;
     float ih, il;
     split_dbl(inv_lam, ih, il);
@@ -1348,6 +1405,11 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
             }
           }
           store8_slices(B3[0].q, plane, (size_t)i * LD + j0, mh, ml, e_m);
+          if (Mf) {
+            float4* mf = reinterpret_cast<float4*>(Mf + (size_t)i * mp + j0);
+            mf[0] = make_float4(mh[0], mh[1], mh[2], mh[3]);
+            mf[1] = make_float4(mh[4], mh[5], mh[6], mh[7]);
+          }
         }
       }
       nrm = warp_sum_f(nrm);
@@ -1358,10 +1420,11 @@ __global__ void __launch_bounds__(ENG == ENG_TC ? TC_THREADS : kThreads,
 
     // lower end of M_0's spectrum: the raw estimate gives the condition estimate
     // lambda_bar / lambda_min(S) = 1 / lambda_min(M_0), half of it steers the steps
-    const float lo_raw = start_lo_slices(B3[0].q, plane, LD, e_m, m, mp,
-                                         reinterpret_cast<float*>(v_s),
-                                         reinterpret_cast<float*>(w_s),
-                                         reinterpret_cast<float*>(red_s));
+    const float lo_raw =
+        Mf ? start_lo_smem(Mf, m, mp, reinterpret_cast<float*>(v_s),
+                           reinterpret_cast<float*>(w_s), reinterpret_cast<float*>(red_s))
+           : start_lo_slices(B3[0].q, plane, LD, e_m, m, mp, reinterpret_cast<float*>(v_s),
+                             reinterpret_cast<float*>(w_s), reinterpret_cast<float*>(red_s));
     float lo = 0.5f * lo_raw;
 
     // tracked vector (p >= 2): the column y of X (the residual vector u is formed after the
