@@ -3,7 +3,7 @@
 // header).  The O(m^3) rotation updates run on the FP32 units: an FP64 operation costs
 // 64 FP32 operations' time on this GPU, and a double-float rotation update takes about 20
 // FP32 operations for the 2 of FP64.  The O(m) rotation angles per step are computed in
-// FP64.  Same ordering and rotation as jacobi.cuh (round-robin pairs; the symmetric 2x2 Schur
+// double-float too (angle_df).  Same ordering and rotation as jacobi.cuh (round-robin pairs; the symmetric 2x2 Schur
 // decomposition of Golub & Van Loan, Alg. 8.4.1); it stops at off(A) <= 1e-12 ||A||_F or,
 // below 1e-9 ||A||_F, once a sweep shrinks off(A) by less than half (the rounding floor of
 // double-floats; FP64's 1e-14 bound they cannot reach).
@@ -36,6 +36,39 @@ __device__ __forceinline__ float2 rot(float2 c, float2 a, float2 s, float2 b) {
   l = l + (e1 - e2);
   const float r = h + l;
   return make_float2(r, l - (r - h));
+}
+
+// Rotation (c, s) of the symmetric 2 x 2 Schur decomposition (Golub & Van Loan, Alg. 8.4.1)
+// that annihilates apq in [[app, apq], [apq, aqq]], as double-floats without FP64: the
+// tangent t comes from FP32 arithmetic on the leading words (an angle off by ~1e-7 leaves
+// a residual of ~1e-7 apq, which the next sweep removes like any other entry), then
+// c = (1 + t^2)^(-1/2) by one double-float Newton step from rsqrtf and s = t c, so that
+// c^2 + s^2 = 1 to ~2^-46 for whatever t: the rotation stays orthogonal.
+__device__ __forceinline__ void angle_df(float2 app, float2 aqq, float2 apq, float2& c,
+                                         float2& s) {
+  if (apq.x == 0.f) {
+    c = make_float2(1.f, 0.f);
+    s = make_float2(0.f, 0.f);
+    return;
+  }
+  const float d = (aqq.x - app.x) + (aqq.y - app.y);
+  const float tau = d / (2.f * apq.x);
+  const float at = fabsf(tau);
+  const float t = at > 1e18f ? 0.5f / tau
+                             : copysignf(1.f, tau) / (at + sqrtf(fmaf(tau, tau, 1.f)));
+  float xh, xl;                                     // x = 1 + t^2 as a double-float
+  const float p = t * t;
+  slc::two_sum(1.f, p, xh, xl);
+  xl += fmaf(t, t, -p);
+  const float r0 = rsqrtf(xh);
+  const float q = r0 * r0, qe = fmaf(r0, r0, -q);   // r0^2 = q + qe exactly
+  const float y = fmaf(xh, q, -1.f) + fmaf(xh, qe, xl * q);   // x r0^2 - 1
+  float ch, cl;
+  slc::two_sum(r0, -0.5f * r0 * y, ch, cl);         // r0 (1 - y / 2)
+  c = make_float2(ch, cl);
+  float sh, sl;
+  slc::two_sum(t * ch, fmaf(t, ch, -(t * ch)) + t * cl, sh, sl);
+  s = make_float2(sh, sl);
 }
 
 // Eigendecomposition of the symmetric m x m matrix A (double-floats, ld m, global) in place:
@@ -78,19 +111,10 @@ static __device__ int jacobi_eig_df(float2* __restrict__ A, float2* __restrict__
         if (k == 0) { p = s; q = mm - 1; }
         else { p = (s + k) % (mm - 1); q = (s - k + mm - 1) % (mm - 1); }
         if (p > q) { const int t = p; p = q; q = t; }
-        double c = 1.0, sn = 0.0;
-        if (q < m) {
-          const double apq = join(A[p * m + q]);
-          if (apq != 0.0) {
-            const double tau = (join(A[q * m + q]) - join(A[p * m + p])) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            sn = t * c;
-          }
-        }
+        float2 cd = make_float2(1.f, 0.f), sd = make_float2(0.f, 0.f);
+        if (q < m) angle_df(A[p * m + p], A[q * m + q], A[p * m + q], cd, sd);
         pair_s[2 * k] = p;
         pair_s[2 * k + 1] = q;
-        const float2 cd = split(c), sd = split(sn);
         cs_s[4 * k] = cd.x;
         cs_s[4 * k + 1] = cd.y;
         cs_s[4 * k + 2] = sd.x;
@@ -184,19 +208,10 @@ static __device__ int jacobi_eig_df_packed(float2* __restrict__ P, float2* __res
         if (k == 0) { p = s; q = mm - 1; }
         else { p = (s + k) % (mm - 1); q = (s - k + mm - 1) % (mm - 1); }
         if (p > q) { const int t = p; p = q; q = t; }
-        double c = 1.0, sn = 0.0;
-        if (q < m) {
-          const double apq = join(P[pidx(p, q, m)]);
-          if (apq != 0.0) {
-            const double tau = (join(P[pidx(q, q, m)]) - join(P[pidx(p, p, m)])) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            sn = t * c;
-          }
-        }
+        float2 cd = make_float2(1.f, 0.f), sd = make_float2(0.f, 0.f);
+        if (q < m) angle_df(P[pidx(p, p, m)], P[pidx(q, q, m)], P[pidx(p, q, m)], cd, sd);
         pair_s[2 * k] = p;
         pair_s[2 * k + 1] = q;
-        const float2 cd = split(c), sd = split(sn);
         cs_s[4 * k] = cd.x;
         cs_s[4 * k + 1] = cd.y;
         cs_s[4 * k + 2] = sd.x;
