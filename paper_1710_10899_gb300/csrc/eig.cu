@@ -71,10 +71,21 @@ __global__ void __launch_bounds__(kThreads) fallback_kernel(FwdArgs a) {
   }
 }
 
-// Packed upper triangle of a submatrix held in shared memory by the backward's Jacobi:
-// orders up to 198 (the rest of the kernel's shared memory and the gather's static row
-// extents leave this much of the 227 KB).
-constexpr int kPackedMax = 198 * 199 / 2;
+// Shared memory of the backward kernel, laid out per row.  Rows of order up to kBwdSmallM:
+// the per-row vectors sized kBwdSmallM, then the upper triangle of the submatrix packed as
+// double-floats (the Jacobi's working matrix) and, when they fit after it (orders up to
+// about 135), the transposed eigenvectors; the gather's row extents use the triangle's
+// space before it is filled.  Larger rows: the vectors sized SUBMAT_MAX_M and the extents;
+// their Jacobi runs in global memory.
+constexpr size_t kBwdSmem = 230400;
+constexpr int kBwdSmallM = 240;
+constexpr size_t kBwdSmallVecBytes =
+    (4 * kBwdSmallM + kRedDoubles) * sizeof(double) + 2 * kBwdSmallM * sizeof(int32_t);
+constexpr int kPackedCap = (int)((kBwdSmem - kBwdSmallVecBytes) / sizeof(float2));
+static_assert((4 * SUBMAT_MAX_M + kRedDoubles) * sizeof(double) +
+                  2 * SUBMAT_MAX_M * sizeof(int32_t) + SUBMAT_MAX_M * sizeof(int2) <=
+              kBwdSmem, "the large-row layout");
+static_assert(kBwdSmallM * (kBwdSmallM + 1) / 2 > kPackedCap, "packed orders end below kBwdSmallM");
 
 // The backward's per-step Jacobi work is latency-bound at 8 warps; 16 warps (128 registers
 // each, the whole register file) hide twice as much.
@@ -83,14 +94,6 @@ static_assert(kBwdThreads / 32 <= kMaxWarps, "reduction scratch");
 
 __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* cs_s = reinterpret_cast<double*>(smem_raw);               // SUBMAT_MAX_M
-  double* al_s = cs_s + SUBMAT_MAX_M;                                 // alpha = lambda^(1/p)
-  double* u_s = al_s + SUBMAT_MAX_M;                                  // V^T g
-  double* w_s = u_s + SUBMAT_MAX_M;                                   // V^T e_pos
-  double* red_s = w_s + SUBMAT_MAX_M;                                 // kRedDoubles
-  int32_t* pair_s = reinterpret_cast<int32_t*>(red_s + kRedDoubles);  // SUBMAT_MAX_M
-  int32_t* R_s = pair_s + SUBMAT_MAX_M;                               // SUBMAT_MAX_M
-  float2* P_s = reinterpret_cast<float2*>(R_s + SUBMAT_MAX_M);        // kPackedMax
   __shared__ int job_s;
   __shared__ int bad_s;
   char* scr = a.scratch + (size_t)blockIdx.x * a.scratch_stride;
@@ -104,20 +107,34 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(BwdArgs a) {
     const int j = a.order[idx];
     if (a.gbuf && (j < a.j0 || j >= a.j1)) continue;     // another wave's row
     const int m = a.m[j], pos = a.pos[j], p = a.p;
+    // this row's shared-memory layout (see kBwdSmem)
+    const bool packed = m * (m + 1) / 2 <= kPackedCap;
+    const int vl = packed ? kBwdSmallM : SUBMAT_MAX_M;
+    double* cs_s = reinterpret_cast<double*>(smem_raw);             // vl
+    double* al_s = cs_s + vl;                                         // alpha = lambda^(1/p)
+    double* u_s = al_s + vl;                                          // V^T g
+    double* w_s = u_s + vl;                                           // V^T e_pos
+    double* red_s = w_s + vl;                                         // kRedDoubles
+    int32_t* pair_s = reinterpret_cast<int32_t*>(red_s + kRedDoubles);   // vl
+    int32_t* R_s = pair_s + vl;                                       // vl
+    float2* P_s = reinterpret_cast<float2*>(R_s + vl);               // kPackedCap (packed)
     double* A = reinterpret_cast<double*>(scr);
     double* V = A + (size_t)m * m;
     double* W = V + (size_t)m * m;
-    gather_dense(a.rowptr, a.colind, a.vals, j, m, R_s, A, red_s);
+    (void)gather_rows(a.rowptr, a.colind, a.vals, j, m, R_s, A, red_s,
+                      reinterpret_cast<int2*>(P_s));                  // extents: m int2
     // the eigendecomposition in double-float (jacobi_df.cuh): with A's upper triangle packed
-    // in shared memory when it fits (eigenvectors transposed in W), else in place in A, V
+    // in shared memory when it fits (eigenvectors transposed after it when they fit too,
+    // else in W), else in place in A, V
     int sweeps;
-    if (m * (m + 1) / 2 <= kPackedMax) {
+    if (packed) {
       for (int e = tid; e < m * m; e += blockDim.x) {
         const int r = e / m, c = e - r * m;
         if (r <= c) P_s[jdf::pidx(r, c, m)] = jdf::split(A[e]);
       }
       __syncthreads();
-      float2* Vt = reinterpret_cast<float2*>(W);
+      const int tri = m * (m + 1) / 2;
+      float2* Vt = tri + m * m <= kPackedCap ? P_s + tri : reinterpret_cast<float2*>(W);
       sweeps = jdf::jacobi_eig_df_packed(P_s, Vt, m, pair_s, reinterpret_cast<float*>(cs_s), red_s);
       for (int e = tid; e < m * m; e += blockDim.x) {
         const int i = e / m, k = e - i * m;
@@ -295,10 +312,7 @@ cudaError_t launch_grad_gather(const int32_t* rowptr, const int32_t* colind, con
 size_t smem_fallback() {
   return (2 * SUBMAT_MAX_M + kRedDoubles) * sizeof(double) + 2 * SUBMAT_MAX_M * sizeof(int32_t);
 }
-size_t smem_backward() {
-  return (4 * SUBMAT_MAX_M + kRedDoubles) * sizeof(double) + 2 * SUBMAT_MAX_M * sizeof(int32_t) +
-         kPackedMax * sizeof(float2);
-}
+size_t smem_backward() { return kBwdSmem; }
 size_t scratch_eig(int mp) { return 3 * (size_t)mp * mp * sizeof(double); }
 
 cudaError_t launch_fallback(const FwdArgs& a, int grid, cudaStream_t s) {

@@ -32,6 +32,28 @@ def test_grad_matches_oracle(sm, p):
     assert np.abs(g - gref).max() <= 1e-10 * np.abs(gref).max()
 
 
+def test_grad_shared_memory_layouts(sm):
+    """Rows whose Jacobi keeps the eigenvectors next to the packed triangle in shared memory
+    (order 100), only the triangle (order 200), or works in global memory (order 260), on
+    one block-diagonal pattern, against the oracle gradient."""
+    import scipy.linalg as sl
+    rng = np.random.default_rng(17)
+    sizes = [100, 200, 260]
+    blocks = []
+    for n in sizes:
+        q = rng.standard_normal((n, n))
+        blocks.append(q @ q.T / n + 0.5 * np.eye(n))
+    a = wl.dense_to_csr(sl.block_diag(*blocks),
+                        keep=sl.block_diag(*[np.ones((n, n), dtype=bool) for n in sizes]))
+    w = wl.random_on_pattern(a, seed=4)
+    plan = sm.submat_plan(a.rowptr, a.colind, 2)
+    sm.submat_invroot(plan, torch.tensor(a.vals, device="cuda"))
+    g = sm.submat_invroot_backward(plan, torch.tensor(w, device="cuda")).cpu().numpy()
+    gref = oracle.grad(a.rowptr, a.colind, a.vals, 2, w)
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) <= 1e-10
+    assert np.abs(g - gref).max() <= 1e-10 * np.abs(gref).max()
+
+
 @pytest.mark.parametrize("p", [2, 3])
 def test_positive_root_grad_matches_oracle(sm, p):
     a = wl.overlap_uniform(n=400, kappa=1e3)
