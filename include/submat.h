@@ -183,8 +183,14 @@ SUBMAT_API submat_status submat_shard_rows(int32_t n, const int32_t* rowptr, int
 /* Fill *opts with the defaults. */
 SUBMAT_API void submat_default_opts(submat_opts* opts);
 
+/* Largest root order of the mixed-precision paths: beyond it the affine term and the
+ * level sums of the integer slices could no longer be kept exact (SUBMAT_PREC_FP64 takes
+ * any p >= 1). */
+#define SUBMAT_MIXED_MAX_P 10
+
 /*
- * Build a plan for A's pattern and the root order p >= 1 (Alg. 1, index part).
+ * Build a plan for A's pattern and the root order p >= 1 (Alg. 1, index part; p at most
+ * SUBMAT_MIXED_MAX_P for the mixed-precision modes, else SUBMAT_EINVAL).
  * Checks the pattern (SUBMAT_EINVAL / ENODIAG / ENOTSYM / ETOOBIG; n > nnz means some row
  * lacks its diagonal: ENODIAG), computes m_j and
  * pos_j on the device, orders the rows by decreasing m_j for the persistent scheduler,

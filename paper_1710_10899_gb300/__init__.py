@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_PKG, "libsubmat.so")
 
 SUBMAT_MAX_M = 1536
 SUBMAT_SMALL_MAX_M = 32
+SUBMAT_MIXED_MAX_P = 10
 PREC_FP64 = 0
 PREC_MIXED_F16 = 1
 PREC_MIXED_F16_SYNC = 2

@@ -335,6 +335,9 @@ static submat_status plan_impl(const submat_csr* csr, int32_t p, const submat_op
   } else if (o.shard_rank < 0 || o.shard_rank >= o.shard_count) {
     return fail(SUBMAT_EINVAL, "shard_rank must lie in [0, shard_count)");
   }
+  if (o.precision != SUBMAT_PREC_FP64 && p > SUBMAT_MIXED_MAX_P)
+    return fail(SUBMAT_EINVAL, "the mixed-precision modes take p <= SUBMAT_MIXED_MAX_P (" +
+                                   std::to_string(SUBMAT_MIXED_MAX_P) + "); use SUBMAT_PREC_FP64");
   if (o.small_max_m < 0) o.small_max_m = kTunedSmallMaxM;
   if (o.sync_max_m < 0) o.sync_max_m = kTunedSyncMaxM;
   if (o.small_max_m > small_engine_max_m())

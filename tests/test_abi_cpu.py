@@ -81,6 +81,11 @@ def test_host_side_validation(lib):
     lib.submat_default_opts(ctypes.byref(o))
     o.grad_deterministic = 2
     assert pkg.STATUS[lib.submat_plan(ctypes.byref(csr), 2, ctypes.byref(o), ctypes.byref(h))] == "SUBMAT_EINVAL"
+    # the mixed modes' largest root order
+    lib.submat_default_opts(ctypes.byref(o))
+    p_big = pkg.SUBMAT_MIXED_MAX_P + 1
+    assert pkg.STATUS[lib.submat_plan(ctypes.byref(csr), p_big, ctypes.byref(o), ctypes.byref(h))] == "SUBMAT_EINVAL"
+    assert b"SUBMAT_PREC_FP64" in lib.submat_last_error()
 
 
 def test_noalloc_host_side_validation(lib):
@@ -193,6 +198,7 @@ def test_binding_constants_match_the_header():
     assert macros["SUBMAT_MAX_M"] == pkg.SUBMAT_MAX_M
     assert macros["SUBMAT_NOALLOC_MAX_M"] == pkg.SUBMAT_NOALLOC_MAX_M
     assert macros["SUBMAT_SMALL_MAX_M"] == pkg.SUBMAT_SMALL_MAX_M
+    assert macros["SUBMAT_MIXED_MAX_P"] == pkg.SUBMAT_MIXED_MAX_P
 
 
 def _prototypes():
