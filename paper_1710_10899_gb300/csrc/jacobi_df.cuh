@@ -275,15 +275,22 @@ static __device__ int jacobi_eig_df_packed(float2* __restrict__ P, float2* __res
       }
       // eigenvectors: rows p, q of Vt, kVtU elements per thread loaded before any is
       // stored (the rows live in global memory: one round trip per kVtU elements)
+      // element e = k m + i of the loop is pair k, row entry i; a thread's elements advance by
+      // blockDim.x, i.e. by dk pairs and di entries (no division per element)
+      const int dk = blockDim.x / m, di = blockDim.x - dk * m;
+      int k_nx = tid / m, i_nx = tid - k_nx * m;
       for (int e0 = tid; e0 < np * m; e0 += kVtU * blockDim.x) {
         float2 vp[kVtU], vq[kVtU];
         int ip[kVtU], iq[kVtU], kk[kVtU];
 #pragma unroll
         for (int u = 0; u < kVtU; ++u) {
           const int e = e0 + u * blockDim.x;
+          const int k = k_nx, i = i_nx;
+          k_nx += dk;
+          i_nx += di;
+          if (i_nx >= m) { i_nx -= m; ++k_nx; }
           kk[u] = -1;
           if (e < np * m) {
-            const int k = e / m, i = e - k * m;
             const int p = pair_s[2 * k], q = pair_s[2 * k + 1];
             if (q < m && cs_s[4 * k + 2] != 0.f) {
               kk[u] = k;
