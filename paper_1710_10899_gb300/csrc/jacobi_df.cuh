@@ -218,16 +218,22 @@ static __device__ int jacobi_eig_df_packed(float2* __restrict__ P, float2* __res
         cs_s[4 * k + 3] = sd.y;
       }
       __syncthreads();
-      // blocks (k, l), k <= l, of the upper block triangle, enumerated row by row:
-      // block t lies in row k with T(k) <= t < T(k+1), T(k) = k (2 np - k + 1) / 2
-      const int nblk = np * (np + 1) / 2;
-      const float b2 = (float)(2 * np + 1);
+      // blocks (k, l), k <= l, of the upper block triangle, folded into rows of np + 1:
+      // folded row r holds block row r (np - r blocks) followed by block row np - 1 - r
+      // (r + 1 blocks); for odd np the middle row holds only its own blocks.  A thread's
+      // blocks advance by blockDim.x, i.e. by dr folded rows and dc places (no division)
+      const int np1 = np + 1;
+      const int nblk = (np / 2) * np1 + ((np & 1) ? np1 / 2 : 0);   // np (np + 1) / 2
+      const int dr = blockDim.x / np1, dc = blockDim.x - dr * np1;
+      int r_nx = tid / np1, c_nx = tid - r_nx * np1;
       for (int e = tid; e < nblk; e += blockDim.x) {
-        int k = (int)((b2 - sqrtf(b2 * b2 - 8.f * (float)e)) * 0.5f);
-        k = max(0, min(k, np - 1));
-        while (k > 0 && k * (2 * np - k + 1) / 2 > e) --k;
-        while (k + 1 < np && (k + 1) * (2 * np - k) / 2 <= e) ++k;
-        const int l = k + (e - k * (2 * np - k + 1) / 2);
+        const int r = r_nx, cc = c_nx;
+        r_nx += dr;
+        c_nx += dc;
+        if (c_nx >= np1) { c_nx -= np1; ++r_nx; }
+        const bool first = cc < np - r;
+        const int k = first ? r : np - 1 - r;
+        const int l = first ? r + cc : k + (cc - (np - r));
         const int pk = pair_s[2 * k], qk = pair_s[2 * k + 1];
         const int pl = pair_s[2 * l], ql = pair_s[2 * l + 1];
         const bool hk = qk < m, hl = ql < m;            // pair has its second index
