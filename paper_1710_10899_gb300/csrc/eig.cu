@@ -194,22 +194,10 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(BwdArgs a) {
       A[e] = gam * 0.5 * (u_s[x] * w_s[y] + w_s[x] * u_s[y]);
     }
     __syncthreads();
-    // W = V Q
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      const int x = e / m, y = e % m;
-      double s = 0.0;
-      for (int k = 0; k < m; ++k) s = fma(V[x * m + k], A[k * m + y], s);
-      W[e] = s;
-    }
-    __syncthreads();
-    // G = W V^T, written over A
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      const int x = e / m, y = e % m;
-      double s = 0.0;
-      for (int k = 0; k < m; ++k) s = fma(W[x * m + k], V[y * m + k], s);
-      A[e] = s;
-    }
-    __syncthreads();
+    // W = V Q, then G = W V^T over A: double-float GEMMs on the FP32 units (jdf::gemm_df),
+    // staged in the shared memory after the row's vectors (the packed triangle is done)
+    jdf::gemm_df<false>(V, A, W, m, P_s);
+    jdf::gemm_df<true>(W, V, A, m, P_s);
     if (a.gbuf) {                // deterministic: keep G_j for the gather pass
       double* gj = a.gbuf + (a.gofs[j] - a.gofs[a.j0]);
       for (int e = tid; e < m * m; e += blockDim.x) gj[e] = A[e];

@@ -324,5 +324,78 @@ static __device__ int jacobi_eig_df_packed(float2* __restrict__ P, float2* __res
   return sweep;
 }
 
+// C = A op(B) for m x m FP64 matrices in global memory (row-major, ld m; op(B) = B, or B^T
+// with TB), accumulated as double-floats on the FP32 units: the leading products error-free
+// through FMA, the cross terms in FP32, the pair renormalised after every product (about 46
+// bits).  64 x 64 output tiles over 16-wide k-slices staged in shared memory as (hi, lo)
+// pairs; 512 threads, 2 x 4 outputs each.  sm: (16 * 65 + 16 * 64) float2 of shared memory.
+// C must not overlap A or B.
+constexpr int kGdTile = 64, kGdK = 16, kGdLdA = kGdTile + 1;
+template <bool TB>
+__device__ void gemm_df(const double* __restrict__ A, const double* __restrict__ B,
+                        double* __restrict__ C, int m, float2* sm) {
+  float2* As = sm;                                  // [kGdK][kGdLdA]: As[kk][ii] = A(i0+ii, k0+kk)
+  float2* Bs = sm + kGdK * kGdLdA;                  // [kGdK][kGdTile]: Bs[kk][jj] = op(B)(k0+kk, j0+jj)
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;   // ty in 0..31
+  const int nt = (m + kGdTile - 1) / kGdTile;
+  for (int t = 0; t < nt * nt; ++t) {
+    const int i0 = (t / nt) * kGdTile, j0 = (t % nt) * kGdTile;
+    float hi[2][4], lo[2][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) hi[r][c] = lo[r][c] = 0.f;
+    for (int k0 = 0; k0 < m; k0 += kGdK) {
+      for (int q = tid; q < kGdK * kGdTile; q += blockDim.x) {
+        {   // A: consecutive threads along k (contiguous in memory)
+          const int ii = q / kGdK, kk = q - ii * kGdK;
+          const int i = i0 + ii, k = k0 + kk;
+          As[kk * kGdLdA + ii] = split(i < m && k < m ? A[(size_t)i * m + k] : 0.0);
+        }
+        if (TB) {   // B^T(k, j) = B(j, k): consecutive threads along k
+          const int jj = q / kGdK, kk = q - jj * kGdK;
+          const int j = j0 + jj, k = k0 + kk;
+          Bs[kk * kGdTile + jj] = split(j < m && k < m ? B[(size_t)j * m + k] : 0.0);
+        } else {    // B(k, j): consecutive threads along j
+          const int kk = q / kGdTile, jj = q - kk * kGdTile;
+          const int j = j0 + jj, k = k0 + kk;
+          Bs[kk * kGdTile + jj] = split(j < m && k < m ? B[(size_t)k * m + j] : 0.0);
+        }
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < kGdK; ++kk) {
+        float2 av[2], bv[4];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) av[r] = As[kk * kGdLdA + ty + 32 * r];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bv[c] = Bs[kk * kGdTile + tx + 16 * c];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float pr = av[r].x * bv[c].x;
+            float e = fmaf(av[r].x, bv[c].x, -pr);
+            e = fmaf(av[r].x, bv[c].y, fmaf(av[r].y, bv[c].x, e));
+            float sh, u;
+            slc::two_sum(hi[r][c], pr, sh, u);
+            u = u + (lo[r][c] + e);
+            hi[r][c] = sh + u;
+            lo[r][c] = u - (hi[r][c] - sh);
+          }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = i0 + ty + 32 * r, j = j0 + tx + 16 * c;
+        if (i < m && j < m) C[(size_t)i * m + j] = (double)hi[r][c] + (double)lo[r][c];
+      }
+  }
+  __syncthreads();
+}
+
 }  // namespace jdf
 }  // namespace submat
