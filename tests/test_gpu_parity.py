@@ -173,6 +173,21 @@ def test_engine_buckets(sm, buckets):
     assert rep["n_fallback"] == 0 and rep["n_rows"] == a.n
 
 
+@pytest.mark.parametrize("p", [4, 7, 10])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_higher_root_orders(sm, p, precision):
+    """Roots beyond the paper's p <= 3, up to the mixed modes' limit SUBMAT_MIXED_MAX_P: the
+    exponent bias grows with p (alpha' = alpha 2^(9-b) must stay an FP16 integer), so these
+    rows run with fewer bits than p = 2's."""
+    assert p <= sm.SUBMAT_MIXED_MAX_P
+    a = wl.overlap_uniform(n=2048)
+    plan, y = run(sm, a, p, precision)
+    rows = sample_rows(a, 100, seed=p)
+    ref = oracle.invroot(a.rowptr, a.colind, a.vals, p, rows=rows)
+    assert row_errors(a, y, ref, rows).max() <= TOL[precision]
+    assert plan.report()["n_notspd"] == 0
+
+
 def test_dense_pattern_equals_full_root(sm):
     import scipy.linalg as sl
     rng = np.random.default_rng(9)
