@@ -821,7 +821,7 @@ __device__ bool gemm_tc(const TcCtx& c, TcState& st, Mat A, Mat B, Mat C, Mat Y,
       const int nch = nw / 8;
       // tile-uniform: do any of its columns reach a later row block (mirror images)?
       const bool tile_mirror = (tn * TC_N + nw - 1) / TC_M > tm;
-      // phase 1: w = acc0 + 2^-8 acc1 + 2^-16 acc2 (error-free sums) + (levels 3, 4) as a
+      // phase 1: w = acc0 + 2^-10 acc1 + 2^-20 acc2 (error-free sums) + 2^-30 acc3 as a
       // double-float into the staging units of row rt.  Level 2 must not be rounded to
       // FP32: when a matrix's entries lie far below its power-of-two scale (or the affine
       // term cancels level 0), levels 0 and 1 are nearly empty and level 2 carries the value
