@@ -55,7 +55,7 @@
 //              tensor path, kept as the baseline the tcgen05 engine is measured against).
 //
 // Working matrices live in a per-CTA global scratch: 29 planes of LD x LD halves per CTA
-// (LD = the plan's largest order padded to 16, at least 128): two X buffers (p = 1), three
+// (LD = the plan's largest order padded to 64, at least 128): two X buffers (p = 1), three
 // buffers for M_k and the partial products and one spare, 4 planes each, the gathered S_j
 // in FP64 in four planes' space, and one plane for the carried vectors.  A submatrix of order m uses the
 // leading mp x mp block (mp = m padded to 16 for tcgen05, 64 for mma.sync); its padding
